@@ -1,0 +1,205 @@
+/*
+ * bfm.h -- C ABI of the GB300 back-and-forth optimal-transport library.
+ *
+ * The back-and-forth method (BFM) of Jacobs & Leger, "A fast approach to
+ * optimal transport: the back-and-forth method" (arXiv 1905.12154) solves the
+ * quadratic-cost Kantorovich dual problem (Section 3, eq. (dual)) between two
+ * densities mu and nu on a regular grid over [0,1]^d (Section 4.3), by
+ * alternating H1-dot gradient ascent steps on J (phi-space) and I (psi-space)
+ * with c-transforms in between (Algorithm 1) and the step-size rule of
+ * Section 4.2.
+ *
+ * Conventions shared by every entry point
+ *   grid      cell-centred, n[a] cells on axis a (2 <= n[a]), ndim in {2, 3};
+ *             cell i of axis a has centre (i + 1/2) / n[a].
+ *   layout    a field is N = n[0]*n[1]*n[2] contiguous elements with axis 0
+ *             fastest: index = (k*n[1] + j)*n[0] + i.  A map is ndim fields
+ *             stored one after the other (component a at offset a*N).
+ *   precision BFM_FP32: fields are float, all reductions, the dual value,
+ *             the residual and the step-size test are FP64.  BFM_FP64: fields
+ *             are double.
+ *   densities non-negative density values; a density of unit mass has
+ *             mean 1 over the grid.  The transport cost C (Section 4.3) is
+ *             half the squared Wasserstein distance: W2^2 = 2 C.
+ *   memory    every field pointer is DEVICE memory owned by the caller unless
+ *             the argument says "host".  The library never allocates device
+ *             memory: scratch comes from a caller-provided device workspace
+ *             of at least the size the matching *_workspace_bytes() returns
+ *             (256-byte aligned).  Work is stream-ordered on `stream`
+ *             (a cudaStream_t passed as void*, NULL = legacy default stream);
+ *             functions that return results to host memory synchronise that
+ *             stream before returning.
+ *   errors    every call returns a bfm_status; on BFM_ERR_INVALID_ARG /
+ *             BFM_ERR_UNSUPPORTED nothing was launched; on BFM_ERR_CUDA the
+ *             CUDA error string is available from bfm_last_error().
+ *   sizes     FFT-based steps need every n[a] of the form 2^p 3^q with
+ *             2 <= n[a] <= 8192 (4096 in FP64); other sizes give
+ *             BFM_ERR_UNSUPPORTED.  The c-transform accepts any 2 <= n[a] <= 8192.
+ */
+#ifndef BFM_H
+#define BFM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BFM_OK = 0,
+    BFM_NOT_CONVERGED = 1,      /* max_iter reached; results are filled */
+    BFM_ERR_INVALID_ARG = -1,   /* bad pointer, size, density (negative, NaN, zero mass) */
+    BFM_ERR_NONFINITE = -2,     /* a reduction produced Inf/NaN during the solve */
+    BFM_ERR_CUDA = -3,          /* a CUDA call failed; see bfm_last_error() */
+    BFM_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up */
+    BFM_ERR_UNSUPPORTED = -5,   /* grid size / cost / precision not supported */
+    BFM_ERR_WORKSPACE = -6      /* workspace NULL, misaligned or too small */
+} bfm_status;
+
+typedef enum { BFM_FP32 = 0, BFM_FP64 = 1 } bfm_precision;
+
+/* Only the quadratic cost |x-y|^2/2 of Section 4.3 is implemented. */
+typedef enum { BFM_COST_QUADRATIC = 0 } bfm_cost;
+
+typedef struct {
+    int ndim;       /* 2 or 3 */
+    int n[3];       /* cells per axis; n[2] ignored when ndim == 2 */
+} bfm_grid;
+
+/* Step-size rule of Section 4.2 and loop control.  bfm_default_options()
+ * fills the paper's values: beta1 = 1/4, beta2 = 3/4, alpha1 = 5/4,
+ * alpha2 = 4/5, sigma0 <= 0 meaning 8 min(1/|mu|_inf, 1/|nu|_inf),
+ * sigma_min = 0.01. */
+typedef struct {
+    double beta1, beta2, alpha1, alpha2;
+    double sigma0;
+    double sigma_min;
+    int poll_every;          /* host reads the device convergence flag every k iterations (default 4) */
+    int warm_start;          /* nonzero: result->phi holds the initial phi on entry (else phi_0 = 0) */
+} bfm_options;
+
+typedef struct {
+    /* outputs the caller provides (DEVICE, precision of the call):
+     *   phi  N elements    the final phi_n (nu side potential)
+     *   psi  N elements    phi_n^c (mu side potential)
+     *   map  ndim*N        T(x) = x - grad psi(x) in [0,1] coordinates (may be NULL) */
+    void *phi, *psi, *map;
+    /* per-iteration logs the caller provides (HOST, length max_iter+1, may be NULL):
+     *   dual[n]  = J(phi_n)  (eq. (defJ)), resid[n] = relative H^-1 residual
+     *   ||nu - T_phi_n # mu|| / ||nu - 1||, sigma[n] = step size at iteration n */
+    double *dual, *resid, *sigma;
+    /* filled by the call */
+    double w2sq;             /* 2 J(phi_final) */
+    double mass_mu, mass_nu; /* input masses (mean * 1): the solve uses mu/mass_mu, nu/mass_nu */
+    double max_mu, max_nu;   /* |mu|_inf, |nu|_inf after normalisation (max density ratio) */
+    double sigma_final;
+    int iters;               /* completed back-and-forth iterations */
+    int converged;
+} bfm_result;
+
+/* ----------------------------------------------------------------------- */
+
+/* Fills `opt` with the paper's step-rule constants (Section 4.2). */
+void bfm_default_options(bfm_options *opt);
+
+/* Human-readable name of a status code (static string). */
+const char *bfm_status_string(bfm_status s);
+
+/* Text of the last CUDA error seen by this thread's calls (static buffer). */
+const char *bfm_last_error(void);
+
+/* Device workspace bytes bfm_solve needs for this grid, precision and
+ * max_iter (log arrays are max_iter+1 long).  0 for an invalid grid. */
+size_t bfm_workspace_bytes(const bfm_grid *grid, bfm_precision prec, int max_iter);
+
+/*
+ * Algorithm 1 (the back-and-forth method) with the step-size rule of
+ * Section 4.2, quadratic cost.  Per iteration n (4 c-transforms and 2
+ * Poisson solves, as counted in Section 4.3):
+ *   phi-half: psi~ = phi^c; J(phi) (eq. (defJ)); rho = T_phi # mu with
+ *             T(x) = x - grad psi~ (Lemma 2.2(ii), Lemma 3.1); g =
+ *             (-Delta)^{-1}(nu - rho) (eq. (gradients_J_I)); residual r_n;
+ *             stop if r_n < tol; phi += sigma g; psi = phi^c; step rule.
+ *   psi-half: the same with mu <-> nu, phi <-> psi, J -> I (eq. (defI)).
+ * mu, nu: DEVICE, N elements each, non-negative, finite, positive mass (not
+ * modified).  tol: stop when the residual drops below it (0 = run max_iter).
+ * out->phi/psi/map: DEVICE outputs (see bfm_result).  opt may be NULL.
+ * Returns BFM_OK (converged), BFM_NOT_CONVERGED (max_iter reached), or an
+ * error.  Synchronises `stream` before returning.
+ */
+bfm_status bfm_solve(const void *mu, const void *nu, const bfm_grid *grid, bfm_cost cost,
+                     bfm_precision prec, double tol, int max_iter, const bfm_options *opt,
+                     void *workspace, size_t workspace_bytes, void *stream, bfm_result *out);
+
+/* Workspace bytes for bfm_solve_host: bfm_workspace_bytes plus device room
+ * for mu, nu, phi, psi and the map. */
+size_t bfm_workspace_bytes_host(const bfm_grid *grid, bfm_precision prec, int max_iter);
+
+/*
+ * bfm_solve with HOST inputs and outputs: copies mu, nu (host, N elements)
+ * into the device workspace, solves, and copies phi, psi (N each) and map
+ * (ndim*N, may be NULL) back to the host arrays given in out->phi/psi/map.
+ * Same algorithm and return values as bfm_solve.
+ */
+bfm_status bfm_solve_host(const void *mu, const void *nu, const bfm_grid *grid, bfm_cost cost,
+                          bfm_precision prec, double tol, int max_iter, const bfm_options *opt,
+                          void *workspace, size_t workspace_bytes, void *stream, bfm_result *out);
+
+/*
+ * The grid c-transform for the quadratic cost (Definition 2.1; Section 4.1):
+ *     out(x) = min over grid points y of |x - y|^2 / 2 - phi(y),
+ * computed by dimension splitting into exact 1-D lower envelopes along each
+ * axis in turn (Section 4.1).  phi, out: DEVICE, N elements; out may equal
+ * phi (in place).  Needs no workspace.
+ */
+bfm_status bfm_ctransform(const void *phi, void *out, const bfm_grid *grid,
+                          bfm_precision prec, void *stream);
+
+/* Workspace bytes for bfm_poisson (twiddle and eigenvalue tables, partial sums). */
+size_t bfm_poisson_workspace_bytes(const bfm_grid *grid, bfm_precision prec);
+
+/*
+ * Neumann Poisson solve of Lemma 2.3 / eq. (gradients_J_I):
+ *     g = (-Delta_h)^{-1} (f - mean f),
+ * Delta_h the 5/7-point Laplacian with reflected ghost cells, diagonalised by
+ * DCT-II along every axis (Section 4.3 inverts the Laplacian by FFT); the
+ * zero mode is set to 0.  f, g: DEVICE, N elements (g may equal f).
+ * G_out (HOST, may be NULL) receives ||f - mean f||^2_{H^-1} = ||g||^2_{H1-dot}
+ * (eq. (defHm1dot)) in FP64; when it is non-NULL the stream is synchronised.
+ */
+bfm_status bfm_poisson(const void *f, void *g, const bfm_grid *grid, bfm_precision prec,
+                       double *G_out, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * The map of Lemma 2.2(ii) for the quadratic cost, T(x) = x - grad psi(x),
+ * with grad psi by central differences (one-sided at the first and last cell
+ * of each line) and T clamped to the box of cell centres.
+ * psi: DEVICE, N elements; map: DEVICE, ndim*N elements ([0,1] coordinates).
+ */
+bfm_status bfm_map(const void *psi, void *map, const bfm_grid *grid, bfm_precision prec,
+                   void *stream);
+
+/*
+ * Pushforward rho = T # mu (Section 2.1; the first variation of Lemma 3.1)
+ * with T(x) = x - grad psi(x) as in bfm_map, discretised by depositing the
+ * mass of every cell with mu != 0 onto the 2^d cell centres around T(x) with
+ * bilinear / trilinear weights.  psi, mu: DEVICE, N elements; rho: DEVICE,
+ * N elements, overwritten (density values: mass is conserved).
+ */
+bfm_status bfm_pushforward(const void *psi, const void *mu, void *rho, const bfm_grid *grid,
+                           bfm_precision prec, void *stream);
+
+/*
+ * Displacement interpolation of Section 4.3 (images):
+ *     rho_t = (S_t) # mu,   S_t(x) = t T(x) + (1 - t) x,
+ * deposited as in bfm_pushforward.  map: DEVICE, ndim*N ([0,1] coordinates,
+ * as bfm_map / bfm_solve write it); mu, rho: DEVICE, N elements; 0 <= t <= 1.
+ */
+bfm_status bfm_interpolate(const void *map, const void *mu, double t, void *rho,
+                           const bfm_grid *grid, bfm_precision prec, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFM_H */

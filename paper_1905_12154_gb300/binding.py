@@ -1,0 +1,334 @@
+"""Thin Python binding of the C ABI in include/bfm.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+libbfm.so.  Functions carry the C names.  Fields are torch CUDA tensors in the
+library's layout (C-order shape (n1, n0) in 2D or (n2, n1, n0) in 3D, axis 0
+fastest), float32 (BFM_FP32) or float64 (BFM_FP64), contiguous.  Work is
+enqueued on torch's current CUDA stream.  There is no CPU fallback: if the
+library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbfm.so")
+
+BFM_OK = 0
+BFM_NOT_CONVERGED = 1
+BFM_ERR_INVALID_ARG = -1
+BFM_ERR_NONFINITE = -2
+BFM_ERR_CUDA = -3
+BFM_ERR_TIMEOUT = -4
+BFM_ERR_UNSUPPORTED = -5
+BFM_ERR_WORKSPACE = -6
+BFM_FP32 = 0
+BFM_FP64 = 1
+BFM_COST_QUADRATIC = 0
+
+
+class bfm_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3)]
+
+
+class bfm_options(ctypes.Structure):
+    _fields_ = [("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double),
+                ("sigma0", ctypes.c_double), ("sigma_min", ctypes.c_double),
+                ("poll_every", ctypes.c_int), ("warm_start", ctypes.c_int)]
+
+
+class bfm_result(ctypes.Structure):
+    _fields_ = [("phi", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("map", ctypes.c_void_p),
+                ("dual", ctypes.POINTER(ctypes.c_double)),
+                ("resid", ctypes.POINTER(ctypes.c_double)),
+                ("sigma", ctypes.POINTER(ctypes.c_double)),
+                ("w2sq", ctypes.c_double), ("mass_mu", ctypes.c_double),
+                ("mass_nu", ctypes.c_double), ("max_mu", ctypes.c_double),
+                ("max_nu", ctypes.c_double), ("sigma_final", ctypes.c_double),
+                ("iters", ctypes.c_int), ("converged", ctypes.c_int)]
+
+
+class BfmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)}" + (f" ({detail})" if detail else ""))
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_GP = ctypes.POINTER(bfm_grid)
+_SIGS = {
+    "bfm_default_options": (None, [ctypes.POINTER(bfm_options)]),
+    "bfm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "bfm_last_error": (ctypes.c_char_p, []),
+    "bfm_workspace_bytes": (ctypes.c_size_t, [_GP, ctypes.c_int, ctypes.c_int]),
+    "bfm_workspace_bytes_host": (ctypes.c_size_t, [_GP, ctypes.c_int, ctypes.c_int]),
+    "bfm_poisson_workspace_bytes": (ctypes.c_size_t, [_GP, ctypes.c_int]),
+    "bfm_solve": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_int, ctypes.POINTER(bfm_options), _P, ctypes.c_size_t,
+                                 _P, ctypes.POINTER(bfm_result)]),
+    "bfm_solve_host": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_int, ctypes.POINTER(bfm_options), _P,
+                                      ctypes.c_size_t, _P, ctypes.POINTER(bfm_result)]),
+    "bfm_ctransform": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, _P]),
+    "bfm_poisson": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   _P, ctypes.c_size_t, _P]),
+    "bfm_map": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, _P]),
+    "bfm_pushforward": (ctypes.c_int, [_P, _P, _P, _GP, ctypes.c_int, _P]),
+    "bfm_interpolate": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _GP, ctypes.c_int, _P]),
+}
+
+
+def lib():
+    """The loaded libbfm.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                                   "(there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().bfm_status_string(int(s)).decode()
+
+
+def last_error() -> str:
+    return lib().bfm_last_error().decode()
+
+
+def _check(s: int, where: str, ok=(BFM_OK,)):
+    if s not in ok:
+        raise BfmError(s, where, last_error() if s == BFM_ERR_CUDA or s < 0 else "")
+    return s
+
+
+# --- marshalling helpers -------------------------------------------------------
+
+def grid_of(shape) -> bfm_grid:
+    n = list(reversed(tuple(shape)))
+    if len(n) not in (2, 3):
+        raise ValueError("fields are 2D (n1, n0) or 3D (n2, n1, n0)")
+    g = bfm_grid()
+    g.ndim = len(n)
+    for a in range(3):
+        g.n[a] = n[a] if a < len(n) else 1
+    return g
+
+
+def _prec(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return BFM_FP32
+    if t.dtype == torch.float64:
+        return BFM_FP64
+    raise TypeError("fields must be float32 or float64")
+
+
+def _dev(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _workspace(nbytes: int, device):
+    """A 256-byte aligned device buffer (torch storage, so torch owns it)."""
+    import torch
+    buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf, buf.data_ptr() + off
+
+
+def _user_workspace(buf):
+    """A caller's uint8 CUDA tensor: its 256-aligned start and usable size."""
+    _dev(buf, "workspace")
+    off = (-buf.data_ptr()) % 256
+    return buf, buf.data_ptr() + off, max(0, buf.numel() * buf.element_size() - off)
+
+
+def _options(**kw) -> bfm_options:
+    o = bfm_options()
+    lib().bfm_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+# --- entry points ----------------------------------------------------------------
+
+def bfm_workspace_bytes(shape, prec: int, max_iter: int) -> int:
+    return int(lib().bfm_workspace_bytes(ctypes.byref(grid_of(shape)), prec, max_iter))
+
+
+def bfm_workspace_bytes_host(shape, prec: int, max_iter: int) -> int:
+    return int(lib().bfm_workspace_bytes_host(ctypes.byref(grid_of(shape)), prec, max_iter))
+
+
+def bfm_poisson_workspace_bytes(shape, prec: int) -> int:
+    return int(lib().bfm_poisson_workspace_bytes(ctypes.byref(grid_of(shape)), prec))
+
+
+def bfm_ctransform(phi, out=None):
+    """out = phi^c on the grid (Definition 2.1, Section 4.1)."""
+    import torch
+    _dev(phi, "phi")
+    out = torch.empty_like(phi) if out is None else _dev(out, "out")
+    g = grid_of(phi.shape)
+    _check(lib().bfm_ctransform(phi.data_ptr(), out.data_ptr(), ctypes.byref(g), _prec(phi),
+                                _stream()), "bfm_ctransform")
+    return out
+
+
+def bfm_poisson(f, out=None, want_G: bool = True):
+    """g = (-Delta)^{-1}(f - mean f) with Neumann conditions (Lemma 2.3); returns (g, G)."""
+    import torch
+    _dev(f, "f")
+    out = torch.empty_like(f) if out is None else _dev(out, "out")
+    g = grid_of(f.shape)
+    prec = _prec(f)
+    nb = lib().bfm_poisson_workspace_bytes(ctypes.byref(g), prec)
+    keep, ws = _workspace(nb, f.device)
+    G = ctypes.c_double(0.0)
+    _check(lib().bfm_poisson(f.data_ptr(), out.data_ptr(), ctypes.byref(g), prec,
+                             ctypes.byref(G) if want_G else None, ws, nb, _stream()),
+           "bfm_poisson")
+    del keep
+    return out, (G.value if want_G else None)
+
+
+def bfm_map(psi, out=None):
+    """T(x) = x - grad psi(x) (Lemma 2.2(ii)); shape (ndim, *grid)."""
+    import torch
+    _dev(psi, "psi")
+    nd = psi.dim()
+    out = torch.empty((nd,) + tuple(psi.shape), dtype=psi.dtype, device=psi.device) if out is None else _dev(out, "out")
+    g = grid_of(psi.shape)
+    _check(lib().bfm_map(psi.data_ptr(), out.data_ptr(), ctypes.byref(g), _prec(psi), _stream()),
+           "bfm_map")
+    return out
+
+
+def bfm_pushforward(psi, mu, out=None):
+    """rho = (x - grad psi) # mu with multilinear deposit (Section 2.1, Lemma 3.1)."""
+    import torch
+    _dev(psi, "psi"); _dev(mu, "mu")
+    out = torch.empty_like(mu) if out is None else _dev(out, "out")
+    g = grid_of(mu.shape)
+    _check(lib().bfm_pushforward(psi.data_ptr(), mu.data_ptr(), out.data_ptr(), ctypes.byref(g),
+                                 _prec(mu), _stream()), "bfm_pushforward")
+    return out
+
+
+def bfm_interpolate(tmap, mu, t: float, out=None):
+    """rho_t = ((1-t) x + t T) # mu (displacement interpolation, Section 4.3)."""
+    import torch
+    _dev(tmap, "map"); _dev(mu, "mu")
+    out = torch.empty_like(mu) if out is None else _dev(out, "out")
+    g = grid_of(mu.shape)
+    _check(lib().bfm_interpolate(tmap.data_ptr(), mu.data_ptr(), float(t), out.data_ptr(),
+                                 ctypes.byref(g), _prec(mu), _stream()), "bfm_interpolate")
+    return out
+
+
+def bfm_solve(mu, nu, tol: float = 1e-6, max_iter: int = 300, with_map: bool = True,
+              phi_init=None, workspace=None, **opts) -> dict:
+    """Algorithm 1 with the Section 4.2 step rule; returns phi, psi, map, w2sq,
+    iters, converged, status and the per-iteration dual / resid / sigma logs."""
+    import torch
+    _dev(mu, "mu"); _dev(nu, "nu")
+    if mu.shape != nu.shape or mu.dtype != nu.dtype:
+        raise ValueError("mu and nu must have the same shape and dtype")
+    g = grid_of(mu.shape)
+    prec = _prec(mu)
+    nd = mu.dim()
+    phi = torch.empty_like(mu)
+    if phi_init is not None:
+        phi.copy_(phi_init)
+        opts["warm_start"] = 1
+    psi = torch.empty_like(mu)
+    tmap = torch.empty((nd,) + tuple(mu.shape), dtype=mu.dtype, device=mu.device) if with_map else None
+    L = max_iter + 1
+    dual = np.zeros(L); resid = np.zeros(L); sig = np.zeros(L)
+    res = bfm_result()
+    res.phi = phi.data_ptr(); res.psi = psi.data_ptr()
+    res.map = tmap.data_ptr() if with_map else None
+    res.dual = dual.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    res.resid = resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    res.sigma = sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    nb = lib().bfm_workspace_bytes(ctypes.byref(g), prec, max_iter)
+    if workspace is None:
+        keep, ws = _workspace(nb, mu.device)
+    else:
+        keep, ws, nb = _user_workspace(workspace)
+    o = _options(**opts)
+    s = lib().bfm_solve(mu.data_ptr(), nu.data_ptr(), ctypes.byref(g), BFM_COST_QUADRATIC, prec,
+                        float(tol), int(max_iter), ctypes.byref(o), ws, nb, _stream(),
+                        ctypes.byref(res))
+    _check(s, "bfm_solve", ok=(BFM_OK, BFM_NOT_CONVERGED))
+    it = res.iters
+    del keep
+    return dict(phi=phi, psi=psi, map=tmap, w2sq=res.w2sq, iters=it, converged=bool(res.converged),
+                status=s, mass_mu=res.mass_mu, mass_nu=res.mass_nu, max_mu=res.max_mu,
+                max_nu=res.max_nu, sigma_final=res.sigma_final, dual=dual[:it + 1].copy(),
+                resid=resid[:it + 1].copy(), sigma=sig[:it + 1].copy())
+
+
+def bfm_solve_host(mu: np.ndarray, nu: np.ndarray, tol: float = 1e-6, max_iter: int = 300,
+                   with_map: bool = True, workspace=None, device=None, **opts) -> dict:
+    """bfm_solve on host (numpy) arrays: the library copies the inputs to the
+    device workspace and the results back."""
+    import torch
+    dt = np.float32 if mu.dtype == np.float32 else np.float64
+    prec = BFM_FP32 if dt == np.float32 else BFM_FP64
+    mu = np.ascontiguousarray(mu, dtype=dt); nu = np.ascontiguousarray(nu, dtype=dt)
+    g = grid_of(mu.shape)
+    nd = mu.ndim
+    phi = np.empty_like(mu); psi = np.empty_like(mu)
+    tmap = np.empty((nd,) + mu.shape, dtype=dt) if with_map else None
+    L = max_iter + 1
+    dual = np.zeros(L); resid = np.zeros(L); sig = np.zeros(L)
+    res = bfm_result()
+    res.phi = phi.ctypes.data; res.psi = psi.ctypes.data
+    res.map = tmap.ctypes.data if with_map else None
+    res.dual = dual.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    res.resid = resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    res.sigma = sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    nb = lib().bfm_workspace_bytes_host(ctypes.byref(g), prec, max_iter)
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if workspace is None:
+        keep, ws = _workspace(nb, dev)
+    else:
+        keep, ws, nb = _user_workspace(workspace)
+    o = _options(**opts)
+    s = lib().bfm_solve_host(mu.ctypes.data, nu.ctypes.data, ctypes.byref(g), BFM_COST_QUADRATIC,
+                             prec, float(tol), int(max_iter), ctypes.byref(o), ws, nb, _stream(),
+                             ctypes.byref(res))
+    _check(s, "bfm_solve_host", ok=(BFM_OK, BFM_NOT_CONVERGED))
+    it = res.iters
+    del keep
+    return dict(phi=phi, psi=psi, map=tmap, w2sq=res.w2sq, iters=it, converged=bool(res.converged),
+                status=s, dual=dual[:it + 1].copy(), resid=resid[:it + 1].copy(),
+                sigma=sig[:it + 1].copy(), max_mu=res.max_mu, max_nu=res.max_nu)

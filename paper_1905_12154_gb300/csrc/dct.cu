@@ -1,0 +1,445 @@
+// dct.cu -- DCT-II / DCT-III along grid lines and the Neumann Poisson solve.
+//
+// The H1-dot gradient of Lemma 2.3 is g = (-Delta)^{-1}(f - mean f) with zero
+// Neumann conditions; the paper inverts the Laplacian with FFTs (Section 4.3).
+// On the cell-centred grid the Laplacian with reflected ghost cells is
+// diagonalised by the DCT-II along every axis, with eigenvalues
+//     lambda_k = sum_a 4 n_a^2 sin^2(pi k_a / (2 n_a)).
+// Each line transform runs in shared memory: two real lines of a tile are
+// packed into the real and imaginary parts of one complex sequence; the
+// DCT-II is a length-n complex FFT of the even/odd reordering
+// v = (x0, x2, x4, ..., x5, x3, x1) followed by the twiddle e^{-i pi k/(2n)}
+// (Makhoul's construction); the inverse undoes both steps.  The forward FFT
+// is an in-place mixed-radix (2/3/4) decimation-in-time network with a
+// digit-reversed load, the inverse a decimation-in-frequency network whose
+// digit-reversed output is gathered on store.
+//
+// Pass kinds (one launch each):
+//   FWD  f -> DCT-II along the axis (optionally f = base - in on load);
+//   MID  on the last axis: DCT-II, divide by lambda (zero mode -> 0),
+//        accumulate G = ||g||^2_{H1-dot} in FP64, inverse DCT;
+//   INV  inverse DCT along the axis (optionally out = upd + sigma * g).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bfm {
+
+enum { DCT_FWD = 0, DCT_MID = 1, DCT_INV = 2 };
+
+template <typename T>
+struct DctArgs {
+    const T* in;
+    const T* base;            // FWD: value = base - in (optional)
+    T* out;
+    const T* upd;             // INV: out = upd + sigma * value (optional)
+    const double* sigma;      // device scalar used with upd
+    double* part;             // MID: per-CTA partial sums of G
+    const int* done;          // optional skip flag
+    const cx_t<T>* tw;        // e^{-2 pi i j/n}
+    const cx_t<T>* dtw;       // e^{-i pi k/(2n)}
+    const unsigned short* drev;   // digit reversal of the stage radices
+    const double* lam_axis;   // MID: eigenvalues along this axis
+    const double* lam_a0;     // MID: eigenvalues along axis 0 (index of the line)
+    const double* lam_a1;     // MID (3D): eigenvalues along axis 1 (outer index)
+    LineTiles lt;
+    int G;                    // threads per line pair
+    int LDZ;                  // shared leading dimension (complex elements)
+    int nst;
+    int rad[kMaxStages];
+    double gscale;            // MID: 1 / N^2
+};
+
+// r-point DFT, SIGN = -1 forward, +1 inverse
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft_small(int r, C* u)
+{
+    using T = decltype(u[0].x);
+    if (r == 2) {
+        const C a = u[0], b = u[1];
+        u[0] = cadd(a, b);
+        u[1] = csub(a, b);
+    } else if (r == 4) {
+        const C a0 = cadd(u[0], u[2]), a1 = csub(u[0], u[2]);
+        const C b0 = cadd(u[1], u[3]), b1 = csub(u[1], u[3]);
+        C ib1;                      // SIGN * i * b1
+        if (SIGN < 0) { ib1.x = b1.y; ib1.y = -b1.x; }
+        else          { ib1.x = -b1.y; ib1.y = b1.x; }
+        u[0] = cadd(a0, b0);
+        u[2] = csub(a0, b0);
+        u[1] = cadd(a1, ib1);
+        u[3] = csub(a1, ib1);
+    } else {  // r == 3
+        const T s = (T)(SIGN * 0.86602540378443864676);   // sin(2 pi / 3) with sign
+        const C t1 = cadd(u[1], u[2]), t2 = csub(u[1], u[2]);
+        C m; m.x = u[0].x - (T)0.5 * t1.x; m.y = u[0].y - (T)0.5 * t1.y;
+        C it2; it2.x = -s * t2.y; it2.y = s * t2.x;          // s * i * t2
+        u[0] = cadd(u[0], t1);
+        u[1] = cadd(m, it2);
+        u[2] = csub(m, it2);
+    }
+}
+
+template <typename T, int MODE, bool CONTIG>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1) dct_pass_kernel(DctArgs<T> a)
+{
+    using C = cx_t<T>;
+    if (a.done && *a.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* zs = reinterpret_cast<C*>(smem_raw);
+    __shared__ double red[32];
+    const LineTiles& lt = a.lt;
+    const int n = lt.n;
+    const int G = a.G;
+    const int tid = threadIdx.x;
+    const int pp = tid / G, t = tid - pp * G;
+    const int npair_max = (lt.W + 1) / 2;
+    C* z = zs + (size_t)pp * a.LDZ;
+    const T inv_n = (T)1 / (T)n;
+    T sig = (T)0;
+    if (MODE == DCT_INV && a.upd) sig = (T)(*a.sigma);
+    double acc = 0.0;
+
+    for (long long tile = blockIdx.x; tile < lt.ntiles; tile += gridDim.x) {
+        const Tile tl = tile_at(lt, tile);
+        const int np = (tl.wact + 1) / 2;
+        const int total = np * n;
+        // ---- load ------------------------------------------------------------
+        for (int e = tid; e < total; e += blockDim.x) {
+            int q, j;
+            if (CONTIG) { q = e / n; j = e - q * n; }
+            else        { j = e / np; q = e - j * np; }
+            const int la = 2 * q, lb = 2 * q + 1;
+            const long long ada = addr_of(lt, tl, la, j);
+            T xa = a.in[ada];
+            T xb = (T)0;
+            if (lb < tl.wact) xb = a.in[ada + tl.lstride];
+            if (MODE == DCT_FWD && a.base) {
+                xa = a.base[ada] - xa;
+                if (lb < tl.wact) xb = a.base[ada + tl.lstride] - xb;
+            }
+            C v; v.x = xa; v.y = xb;
+            if (MODE == DCT_INV) {
+                zs[(size_t)q * a.LDZ + j] = v;                       // natural order
+            } else {
+                const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
+                zs[(size_t)q * a.LDZ + a.drev[m]] = v;               // DIT input order
+            }
+        }
+        __syncthreads();
+        const bool active = (pp < np);
+        if (MODE != DCT_INV) {
+            // ---- forward DIT FFT ---------------------------------------------
+            int L = 1;
+            for (int s = 0; s < a.nst; ++s) {
+                const int r = a.rad[s];
+                const int Lp = L * r;
+                const int tstep = n / Lp;
+                if (active) {
+                    for (int b = t; b < n / r; b += G) {
+                        const int B = b / L, k1 = b - B * L;
+                        const int base = B * Lp + k1;
+                        C u[4];
+                        for (int q = 0; q < r; ++q) {
+                            C v = z[base + q * L];
+                            if (q) v = cmul(v, a.tw[q * k1 * tstep]);
+                            u[q] = v;
+                        }
+                        dft_small<-1>(r, u);
+                        for (int q = 0; q < r; ++q) z[base + q * L] = u[q];
+                    }
+                }
+                L = Lp;
+                __syncthreads();
+            }
+            // ---- separate the two lines, apply e^{-i pi k/2n} -------------------
+            if (active) {
+                for (int k = t; k <= n / 2; k += G) {
+                    const int km = (n - k) % n;
+                    const C Zk = z[k], Zm = z[km];
+                    // A_k = (Z_k + conj Z_m)/2, B_k = -i (Z_k - conj Z_m)/2
+                    C A, B;
+                    A.x = (T)0.5 * (Zk.x + Zm.x); A.y = (T)0.5 * (Zk.y - Zm.y);
+                    B.x = (T)0.5 * (Zk.y + Zm.y); B.y = (T)0.5 * (Zm.x - Zk.x);
+                    const C dk = a.dtw[k];
+                    C outk; outk.x = dk.x * A.x - dk.y * A.y; outk.y = dk.x * B.x - dk.y * B.y;
+                    if (km != k) {
+                        C Am, Bm;
+                        Am.x = (T)0.5 * (Zm.x + Zk.x); Am.y = (T)0.5 * (Zm.y - Zk.y);
+                        Bm.x = (T)0.5 * (Zm.y + Zk.y); Bm.y = (T)0.5 * (Zk.x - Zm.x);
+                        const C dm = a.dtw[km];
+                        C outm; outm.x = dm.x * Am.x - dm.y * Am.y; outm.y = dm.x * Bm.x - dm.y * Bm.y;
+                        z[km] = outm;
+                    }
+                    z[k] = outk;
+                }
+            }
+            __syncthreads();
+        }
+        if (MODE == DCT_MID) {
+            // ---- divide by the eigenvalues; G = (1/N^2) sum w X^2 / lambda ------------
+            if (active) {
+                const int ia = tl.i0 + 2 * pp, ib = ia + 1;
+                double La = a.lam_a0[ia], Lb = (2 * pp + 1 < tl.wact) ? a.lam_a0[ib] : 0.0;
+                double wa = (ia == 0) ? 1.0 : 2.0, wb = (ib == 0) ? 1.0 : 2.0;
+                if (a.lam_a1) {
+                    const int jo = (int)tl.outer;
+                    La += a.lam_a1[jo]; Lb += a.lam_a1[jo];
+                    const double wo = (jo == 0) ? 1.0 : 2.0;
+                    wa *= wo; wb *= wo;
+                }
+                const bool has_b = (2 * pp + 1 < tl.wact);
+                for (int k = t; k < n; k += G) {
+                    const double lk = a.lam_axis[k];
+                    const double wk = (k == 0) ? 1.0 : 2.0;
+                    C v = z[k];
+                    const double la = La + lk, lb = Lb + lk;
+                    double ga = 0.0, gb = 0.0;
+                    if (la > 0.0) { ga = (double)v.x / la; acc += wa * wk * (double)v.x * ga; }
+                    if (has_b && lb > 0.0) { gb = (double)v.y / lb; acc += wb * wk * (double)v.y * gb; }
+                    v.x = (T)ga; v.y = (T)gb;
+                    z[k] = v;
+                }
+            }
+            __syncthreads();
+        }
+        if (MODE != DCT_FWD) {
+            // ---- combine the two real spectra into one complex sequence -----------
+            if (active) {
+                for (int k = t; k <= n / 2; k += G) {
+                    const int km = (n - k) % n;
+                    const C Xk = z[k], Xm = z[km];
+                    // V_k = e^{i pi k/2n} (X_k - i X_{n-k}), X_n = 0; Z = Va + i Vb
+                    const T xam = (k == 0) ? (T)0 : Xm.x, xbm = (k == 0) ? (T)0 : Xm.y;
+                    const C dk = cconj(a.dtw[k]);
+                    C Va, Vb;
+                    Va.x = dk.x * Xk.x + dk.y * xam; Va.y = dk.y * Xk.x - dk.x * xam;
+                    Vb.x = dk.x * Xk.y + dk.y * xbm; Vb.y = dk.y * Xk.y - dk.x * xbm;
+                    C Zk; Zk.x = Va.x - Vb.y; Zk.y = Va.y + Vb.x;
+                    if (km != k) {
+                        const C dm = cconj(a.dtw[km]);
+                        C Wa, Wb;
+                        Wa.x = dm.x * Xm.x + dm.y * Xk.x; Wa.y = dm.y * Xm.x - dm.x * Xk.x;
+                        Wb.x = dm.x * Xm.y + dm.y * Xk.y; Wb.y = dm.y * Xm.y - dm.x * Xk.y;
+                        C Zm; Zm.x = Wa.x - Wb.y; Zm.y = Wa.y + Wb.x;
+                        z[km] = Zm;
+                    }
+                    z[k] = Zk;
+                }
+            }
+            __syncthreads();
+            // ---- inverse DIF FFT -----------------------------------------------------
+            int Lend = 1;
+            for (int s = 0; s < a.nst; ++s) Lend *= a.rad[s];
+            int L = Lend;
+            for (int s = a.nst - 1; s >= 0; --s) {
+                const int r = a.rad[s];
+                const int Lp = L;
+                L = Lp / r;
+                const int tstep = n / Lp;
+                if (active) {
+                    for (int b = t; b < n / r; b += G) {
+                        const int B = b / L, k1 = b - B * L;
+                        const int base = B * Lp + k1;
+                        C u[4];
+                        for (int q = 0; q < r; ++q) u[q] = z[base + q * L];
+                        dft_small<+1>(r, u);
+                        for (int q = 0; q < r; ++q) {
+                            C v = u[q];
+                            if (q) v = cmul(v, cconj(a.tw[q * k1 * tstep]));
+                            z[base + q * L] = v;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // ---- store ------------------------------------------------------------------
+        for (int e = tid; e < total; e += blockDim.x) {
+            int q, j;
+            if (CONTIG) { q = e / n; j = e - q * n; }
+            else        { j = e / np; q = e - j * np; }
+            const int la = 2 * q, lb = 2 * q + 1;
+            const long long ada = addr_of(lt, tl, la, j);
+            C v;
+            if (MODE == DCT_FWD) {
+                v = zs[(size_t)q * a.LDZ + j];
+            } else {
+                const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
+                v = zs[(size_t)q * a.LDZ + a.drev[m]];
+                v.x *= inv_n;
+                v.y *= inv_n;
+            }
+            if (MODE == DCT_INV && a.upd) {
+                a.out[ada] = a.upd[ada] + sig * v.x;
+                if (lb < tl.wact) a.out[ada + tl.lstride] = a.upd[ada + tl.lstride] + sig * v.y;
+            } else {
+                a.out[ada] = v.x;
+                if (lb < tl.wact) a.out[ada + tl.lstride] = v.y;
+            }
+        }
+        __syncthreads();
+    }
+    if (MODE == DCT_MID && a.part) {
+        const double s = block_sum(acc, red);
+        if (threadIdx.x == 0) a.part[blockIdx.x] = s * a.gscale;
+    }
+    (void)npair_max;
+}
+
+// ---------------------------------------------------------------------------
+// tables: twiddles, digit reversal and eigenvalues (computed on the device in FP64)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void fill_tables_kernel(int n, cx_t<T>* tw, cx_t<T>* dtw, unsigned short* drev,
+                                   double* lam, int nst, FftRadices rs)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)j / (double)n, &s, &c);
+    tw[j].x = (T)c; tw[j].y = (T)s;
+    sincospi(-(double)j / (2.0 * (double)n), &s, &c);
+    dtw[j].x = (T)c; dtw[j].y = (T)s;
+    const double sh = sinpi((double)j / (2.0 * (double)n));
+    lam[j] = 4.0 * (double)n * (double)n * sh * sh;
+    // digit reversal: element m -> position p (DIT with radices rs.r[0..nst))
+    int m = j, p = 0, Lw[kMaxStages];
+    int L = 1;
+    for (int l = 0; l < nst; ++l) { Lw[l] = L; L *= rs.r[l]; }
+    for (int l = nst - 1; l >= 0; --l) {
+        const int q = m % rs.r[l];
+        m /= rs.r[l];
+        p += q * Lw[l];
+    }
+    drev[j] = (unsigned short)p;
+}
+
+bool fft_radices(int n, FftRadices* rs)
+{
+    int m = n, k = 0;
+    int twos = 0, fours = 0, threes = 0;
+    while (m % 4 == 0) { ++fours; m /= 4; }
+    while (m % 2 == 0) { ++twos; m /= 2; }
+    while (m % 3 == 0) { ++threes; m /= 3; }
+    if (m != 1) return false;
+    if (twos + fours + threes > kMaxStages) return false;
+    for (int i = 0; i < twos; ++i) rs->r[k++] = 2;
+    for (int i = 0; i < threes; ++i) rs->r[k++] = 3;
+    for (int i = 0; i < fours; ++i) rs->r[k++] = 4;
+    rs->nst = k;
+    return true;
+}
+
+size_t axis_table_bytes(int n, int elem_bytes)
+{
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return up((size_t)n * 2 * elem_bytes) * 2 + up((size_t)n * 2) + up((size_t)n * 8);
+}
+
+template <typename T>
+bfm_status fill_axis_tables(int n, AxisTables* t, unsigned char* ws, cudaStream_t st)
+{
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    FftRadices rs;
+    if (!fft_radices(n, &rs)) return BFM_ERR_UNSUPPORTED;
+    t->n = n;
+    t->rs = rs;
+    t->tw = ws;
+    t->dtw = ws + up((size_t)n * 2 * sizeof(T));
+    t->drev = reinterpret_cast<unsigned short*>(ws + 2 * up((size_t)n * 2 * sizeof(T)));
+    t->lam = reinterpret_cast<double*>(ws + 2 * up((size_t)n * 2 * sizeof(T)) + up((size_t)n * 2));
+    fill_tables_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(
+        n, reinterpret_cast<cx_t<T>*>(t->tw), reinterpret_cast<cx_t<T>*>(t->dtw), t->drev, t->lam,
+        rs.nst, rs);
+    BFM_LAUNCH_CHECK("fill_tables_kernel");
+    return BFM_OK;
+}
+
+template bfm_status fill_axis_tables<float>(int, AxisTables*, unsigned char*, cudaStream_t);
+template bfm_status fill_axis_tables<double>(int, AxisTables*, unsigned char*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// launch planning
+// ---------------------------------------------------------------------------
+DctPlan plan_dct_pass(const Grid& g, int axis, int elem_bytes)
+{
+    DctPlan p;
+    const int n = g.n[axis];
+    const bool contig = (axis == 0);
+    int G = n / 8;
+    if (G < 8) G = 8;
+    if (G > 256) G = 256;
+    G = (G + 7) & ~7;
+    p.G = G;
+    p.LDZ = n + 1;
+    const size_t pair_bytes = (size_t)p.LDZ * 2 * elem_bytes;
+    const size_t budget = 200 * 1024;
+    const int max_threads = elem_bytes == 8 ? 512 : 1024;   // FP64 gets 128 registers
+    int W = 2 * (max_threads / G);
+    while (W > 2 && (size_t)(W / 2) * pair_bytes > budget) W -= 2;
+    if (W > 32) W = 32;
+    if (!contig && W > g.n[0]) W = g.n[0];
+    if (W < 1) W = 1;
+    p.W = W;
+    const int npairs = (W + 1) / 2;
+    p.threads = ((npairs * G + 31) / 32) * 32;      // whole warps; extra threads idle
+    p.smem = (size_t)npairs * pair_bytes;
+    p.tiles = make_tiles(g, axis, W);
+    return p;
+}
+
+template <typename T, int MODE>
+static void* dct_kernel(bool contig)
+{
+    return contig ? (void*)dct_pass_kernel<T, MODE, true> : (void*)dct_pass_kernel<T, MODE, false>;
+}
+
+template <typename T>
+bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* tabs,
+                           const T* in, const T* base, T* out, const T* upd,
+                           const double* sigma, double* part, const int* done,
+                           cudaStream_t st, int* blocks_used)
+{
+    DctPlan p = plan_dct_pass(g, axis, (int)sizeof(T));
+    const AxisTables& tb = tabs[axis];
+    DctArgs<T> a;
+    a.in = in; a.base = base; a.out = out; a.upd = upd; a.sigma = sigma; a.part = part;
+    a.done = done;
+    a.tw = reinterpret_cast<const cx_t<T>*>(tb.tw);
+    a.dtw = reinterpret_cast<const cx_t<T>*>(tb.dtw);
+    a.drev = tb.drev;
+    a.lam_axis = tb.lam;
+    a.lam_a0 = tabs[0].lam;
+    a.lam_a1 = (g.ndim == 3) ? tabs[1].lam : nullptr;
+    a.lt = p.tiles;
+    a.G = p.G;
+    a.LDZ = p.LDZ;
+    a.nst = tb.rs.nst;
+    for (int i = 0; i < kMaxStages; ++i) a.rad[i] = (i < tb.rs.nst) ? tb.rs.r[i] : 0;
+    a.gscale = 1.0 / ((double)g.N * (double)g.N);
+    void* k;
+    const bool contig = (axis == 0);
+    if (mode == DCT_FWD) k = dct_kernel<T, DCT_FWD>(contig);
+    else if (mode == DCT_MID) k = dct_kernel<T, DCT_MID>(contig);
+    else k = dct_kernel<T, DCT_INV>(contig);
+    BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    long long blocks = p.tiles.ntiles;
+    const long long cap = (long long)num_sms() * 4;
+    if (blocks > cap) blocks = cap;
+    if (blocks > kMaxPartials) blocks = kMaxPartials;
+    if (blocks < 1) blocks = 1;
+    void* args[] = {&a};
+    BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(p.threads), args, p.smem, st));
+    if (blocks_used) *blocks_used = (int)blocks;
+    return BFM_OK;
+}
+
+template bfm_status launch_dct_pass<float>(const Grid&, int, int, const AxisTables*, const float*,
+                                           const float*, float*, const float*, const double*,
+                                           double*, const int*, cudaStream_t, int*);
+template bfm_status launch_dct_pass<double>(const Grid&, int, int, const AxisTables*,
+                                            const double*, const double*, double*,
+                                            const double*, const double*, double*, const int*,
+                                            cudaStream_t, int*);
+
+}  // namespace bfm

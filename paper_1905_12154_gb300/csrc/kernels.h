@@ -1,0 +1,66 @@
+// kernels.h -- internal launch interface between the library's .cu files.
+#pragma once
+
+#include "common.cuh"
+
+namespace bfm {
+
+struct CtPlan {
+    int K, G, W, LD, LDI, threads;
+    size_t smem;
+    LineTiles tiles;
+};
+
+struct FftRadices {
+    int nst;
+    int r[kMaxStages];
+};
+
+struct AxisTables {
+    int n;
+    FftRadices rs;
+    void* tw;                 // complex, n
+    void* dtw;                // complex, n
+    unsigned short* drev;     // n
+    double* lam;              // n
+};
+
+struct DctPlan {
+    int G, W, LDZ, threads;
+    size_t smem;
+    LineTiles tiles;
+};
+
+CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes);
+DctPlan plan_dct_pass(const Grid& g, int axis, int elem_bytes);
+
+template <typename T>
+bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool negate,
+                          const T* w_in, double* part_in, const T* w_out, double* part_out,
+                          const int* done, int max_blocks, cudaStream_t st, int* blocks_used);
+
+bool fft_radices(int n, FftRadices* rs);
+size_t axis_table_bytes(int n, int elem_bytes);
+
+template <typename T>
+bfm_status fill_axis_tables(int n, AxisTables* t, unsigned char* ws, cudaStream_t st);
+
+enum { PASS_FWD = 0, PASS_MID = 1, PASS_INV = 2 };
+
+template <typename T>
+bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* tabs,
+                           const T* in, const T* base, T* out, const T* upd,
+                           const double* sigma, double* part, const int* done,
+                           cudaStream_t st, int* blocks_used);
+
+// scatter.cu
+template <typename T>
+bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho,
+                              const int* done, cudaStream_t st);
+template <typename T>
+bfm_status launch_map(const Grid& g, const T* psi, T* map, cudaStream_t st);
+template <typename T>
+bfm_status launch_interpolate(const Grid& g, const T* map, const T* mu, double t, T* rho,
+                              cudaStream_t st);
+
+}  // namespace bfm

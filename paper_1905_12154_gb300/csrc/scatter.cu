@@ -1,0 +1,189 @@
+// scatter.cu -- the map T(x) = x - grad psi(x) and the pushforward T # mu.
+//
+// Lemma 2.2(ii): for the quadratic cost the minimiser of the c-transform is
+// T(x) = x - grad phi^c(x).  Lemma 3.1: the first variation of J is
+// nu - T # mu.  The pushforward (Section 2.1) is discretised by sending the
+// mass of every source cell to the 2^d cell centres around T(x) with
+// multilinear weights; T is clamped to the box of cell centres so mass is
+// conserved.  grad psi uses central differences, one-sided at the first and
+// last cell of a line.  Positions are kept in cell-index units,
+//   pos_a = i_a - (d psi / d x_a) * n_a,
+// which keeps FP32 exact to the rounding of the difference itself.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bfm {
+
+struct GridDev {
+    int n[3];
+    long long s[3];
+    long long N;
+};
+
+static GridDev dev_grid(const Grid& g)
+{
+    GridDev d;
+    for (int a = 0; a < 3; ++a) { d.n[a] = g.n[a]; d.s[a] = g.stride[a]; }
+    d.N = g.N;
+    return d;
+}
+
+// position of T(x) along one axis, in cell-index units, clamped to [0, n-1]
+template <typename T>
+__device__ __forceinline__ T map_pos(const T* psi, long long idx, int i, int n, long long s)
+{
+    T dpos;
+    const T nn = (T)n * (T)n;
+    if (i == 0)          dpos = (psi[idx + s] - psi[idx]) * nn;
+    else if (i == n - 1) dpos = (psi[idx] - psi[idx - s]) * nn;
+    else                 dpos = (psi[idx + s] - psi[idx - s]) * (T)0.5 * nn;
+    T pos = (T)i - dpos;
+    pos = fmin(fmax(pos, (T)0), (T)(n - 1));
+    return pos;
+}
+
+template <typename T, int NDIM>
+__device__ __forceinline__ void deposit(T* rho, const GridDev& g, const T* pos, T m)
+{
+    int i0[3];
+    T w1[3];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        int c = (int)floor(pos[a]);
+        if (c > g.n[a] - 2) c = g.n[a] - 2;
+        if (c < 0) c = 0;
+        i0[a] = c;
+        w1[a] = pos[a] - (T)c;
+    }
+#pragma unroll
+    for (int c = 0; c < (1 << NDIM); ++c) {
+        T w = m;
+        long long q = 0;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const int up = (c >> a) & 1;
+            w *= up ? w1[a] : ((T)1 - w1[a]);
+            q += (long long)(i0[a] + up) * g.s[a];
+        }
+        if (w != (T)0) atomicAdd(rho + q, w);
+    }
+}
+
+template <typename T, int NDIM>
+__global__ void pushforward_kernel(const T* __restrict__ psi, const T* __restrict__ mu,
+                                   T* __restrict__ rho, GridDev g, const int* done)
+{
+    if (done && *done) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
+        const T m = mu[idx];
+        if (m == (T)0) continue;
+        long long r = idx;
+        T pos[3];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const int i = (int)(r % g.n[a]);
+            r /= g.n[a];
+            pos[a] = map_pos(psi, idx, i, g.n[a], g.s[a]);
+        }
+        deposit<T, NDIM>(rho, g, pos, m);
+    }
+}
+
+template <typename T, int NDIM>
+__global__ void map_kernel(const T* __restrict__ psi, T* __restrict__ out, GridDev g)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
+        long long r = idx;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const int i = (int)(r % g.n[a]);
+            r /= g.n[a];
+            const T pos = map_pos(psi, idx, i, g.n[a], g.s[a]);
+            out[a * g.N + idx] = (pos + (T)0.5) / (T)g.n[a];
+        }
+    }
+}
+
+template <typename T, int NDIM>
+__global__ void interpolate_kernel(const T* __restrict__ map, const T* __restrict__ mu, T tt,
+                                   T* __restrict__ rho, GridDev g)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
+        const T m = mu[idx];
+        if (m == (T)0) continue;
+        long long r = idx;
+        T pos[3];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const int i = (int)(r % g.n[a]);
+            r /= g.n[a];
+            const T tpos = map[a * g.N + idx] * (T)g.n[a] - (T)0.5;   // T(x) in index units
+            T p = (T)i + tt * (tpos - (T)i);
+            p = fmin(fmax(p, (T)0), (T)(g.n[a] - 1));
+            pos[a] = p;
+        }
+        deposit<T, NDIM>(rho, g, pos, m);
+    }
+}
+
+static int grid_blocks(long long N, int threads)
+{
+    long long b = (N + threads - 1) / threads;
+    const long long cap = (long long)num_sms() * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename T>
+bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho, const int* done,
+                              cudaStream_t st)
+{
+    BFM_CUDA(cudaMemsetAsync(rho, 0, sizeof(T) * g.N, st));
+    const GridDev d = dev_grid(g);
+    const int th = 256, bl = grid_blocks(g.N, th);
+    if (g.ndim == 2) pushforward_kernel<T, 2><<<bl, th, 0, st>>>(psi, mu, rho, d, done);
+    else             pushforward_kernel<T, 3><<<bl, th, 0, st>>>(psi, mu, rho, d, done);
+    BFM_LAUNCH_CHECK("pushforward_kernel");
+    return BFM_OK;
+}
+
+template <typename T>
+bfm_status launch_map(const Grid& g, const T* psi, T* map, cudaStream_t st)
+{
+    const GridDev d = dev_grid(g);
+    const int th = 256, bl = grid_blocks(g.N, th);
+    if (g.ndim == 2) map_kernel<T, 2><<<bl, th, 0, st>>>(psi, map, d);
+    else             map_kernel<T, 3><<<bl, th, 0, st>>>(psi, map, d);
+    BFM_LAUNCH_CHECK("map_kernel");
+    return BFM_OK;
+}
+
+template <typename T>
+bfm_status launch_interpolate(const Grid& g, const T* map, const T* mu, double t, T* rho,
+                              cudaStream_t st)
+{
+    BFM_CUDA(cudaMemsetAsync(rho, 0, sizeof(T) * g.N, st));
+    const GridDev d = dev_grid(g);
+    const int th = 256, bl = grid_blocks(g.N, th);
+    if (g.ndim == 2) interpolate_kernel<T, 2><<<bl, th, 0, st>>>(map, mu, (T)t, rho, d);
+    else             interpolate_kernel<T, 3><<<bl, th, 0, st>>>(map, mu, (T)t, rho, d);
+    BFM_LAUNCH_CHECK("interpolate_kernel");
+    return BFM_OK;
+}
+
+template bfm_status launch_pushforward<float>(const Grid&, const float*, const float*, float*,
+                                              const int*, cudaStream_t);
+template bfm_status launch_pushforward<double>(const Grid&, const double*, const double*, double*,
+                                               const int*, cudaStream_t);
+template bfm_status launch_map<float>(const Grid&, const float*, float*, cudaStream_t);
+template bfm_status launch_map<double>(const Grid&, const double*, double*, cudaStream_t);
+template bfm_status launch_interpolate<float>(const Grid&, const float*, const float*, double,
+                                              float*, cudaStream_t);
+template bfm_status launch_interpolate<double>(const Grid&, const double*, const double*, double,
+                                               double*, cudaStream_t);
+
+}  // namespace bfm

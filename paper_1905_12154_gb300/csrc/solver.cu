@@ -1,0 +1,676 @@
+// solver.cu -- Algorithm 1 (the back-and-forth method) on one GPU, and the
+// library's C ABI.
+//
+// Per iteration n (Algorithm 1; 4 c-transforms and 2 Poisson solves, the
+// operation count of Section 4.3):
+//   phi-half: psi~ = phi^c and J(phi) = <phi,nu> + <psi~,mu> (eq. (defJ));
+//             rho = T#mu with T = x - grad psi~ (Lemma 2.2(ii), Lemma 3.1);
+//             g = (-Delta)^{-1}(nu - rho) and G = ||g||^2 (eq. (gradients_J_I));
+//             residual r_n = sqrt(G / ||nu - 1||^2_{H^-1}); stop if r_n < tol;
+//             phi += sigma g; psi = phi^c; step rule on J(phi_{n+1/2}) - J(phi_n).
+//   psi-half: the same with mu <-> nu, phi <-> psi and I (eq. (defI)).
+// The step rule (Section 4.2, no backtracking): gain < beta1 sigma G shrinks
+// sigma by alpha2 (not below sigma_min), gain > beta2 sigma G grows it by
+// alpha1.  One sigma is shared by both half steps.
+//
+// Every scalar decision (dual values, residual, step rule, convergence) is
+// taken on the device by one-block FP64 kernels, so the host only enqueues
+// launches and reads the `done` flag every few iterations.  Fields are FP32
+// or FP64; all reductions are FP64 and deterministic for a fixed grid.
+#include <string.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bfm {
+
+struct SolverState {
+    double sigma;
+    double J_old;
+    double G;
+    double Gref;
+    double tol;
+    double beta1, beta2, alpha1, alpha2, sigma_min;
+    double mass_mu, mass_nu, max_mu, max_nu, min_mu, min_nu;
+    double last_resid;
+    int bad_mu, bad_nu;
+    int iter;
+    int max_iter;
+    int done;
+    int converged;
+    int nonfinite;
+    int pad;
+};
+
+struct Logs {
+    double* dual;
+    double* resid;
+    double* sigma;
+};
+
+// ---------------------------------------------------------------------------
+// small FP64 kernels
+// ---------------------------------------------------------------------------
+__device__ double block_sum_parts(const double* p, int n, double* red)
+{
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
+    return block_sum(v, red);
+}
+
+template <typename T>
+__global__ void stats_kernel(const T* __restrict__ x, long long N, double* psum, double* pmax,
+                             double* pmin, double* pbad)
+{
+    __shared__ double red[32];
+    double s = 0.0, mx = -1.0e300, mn = 1.0e300, bad = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double v = (double)x[i];
+        if (!isfinite(v)) bad += 1.0;
+        else { s += v; mx = fmax(mx, v); mn = fmin(mn, v); }
+    }
+    const double ts = block_sum(s, red);
+    const double tb = block_sum(bad, red);
+    const double tmx = block_max(mx, red);
+    const double tmn = -block_max(-mn, red);
+    if (threadIdx.x == 0) {
+        psum[blockIdx.x] = ts; pmax[blockIdx.x] = tmx; pmin[blockIdx.x] = tmn; pbad[blockIdx.x] = tb;
+    }
+}
+
+__global__ void stats_finalize_kernel(SolverState* st, const double* psum, const double* pmax,
+                                      const double* pmin, const double* pbad, int nb, double hd,
+                                      int which)
+{
+    __shared__ double red[32];
+    const double s = block_sum_parts(psum, nb, red);
+    const double b = block_sum_parts(pbad, nb, red);
+    double mx = -1.0e300, mn = 1.0e300;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) { mx = fmax(mx, pmax[i]); mn = fmin(mn, pmin[i]); }
+    mx = block_max(mx, red);
+    mn = -block_max(-mn, red);
+    if (threadIdx.x == 0) {
+        const double mass = s * hd;
+        if (which == 0) { st->mass_mu = mass; st->max_mu = mx; st->min_mu = mn; st->bad_mu = b > 0; }
+        else            { st->mass_nu = mass; st->max_nu = mx; st->min_nu = mn; st->bad_nu = b > 0; }
+    }
+}
+
+template <typename T>
+__global__ void scale_kernel(const T* __restrict__ in, T* __restrict__ out, long long N,
+                             const SolverState* st, int which)
+{
+    const double m = which == 0 ? st->mass_mu : st->mass_nu;
+    const T inv = (T)(1.0 / m);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        out[i] = in[i] * inv;
+}
+
+__global__ void init_state_kernel(SolverState* st, double sigma0, double tol, int max_iter,
+                                  double b1, double b2, double a1, double a2, double smin)
+{
+    if (threadIdx.x != 0) return;
+    const double mxm = st->max_mu / st->mass_mu, mxn = st->max_nu / st->mass_nu;
+    st->max_mu = mxm;
+    st->max_nu = mxn;
+    st->sigma = sigma0 > 0.0 ? sigma0 : 8.0 * fmin(1.0 / mxm, 1.0 / mxn);
+    st->tol = tol;
+    st->max_iter = max_iter;
+    st->beta1 = b1; st->beta2 = b2; st->alpha1 = a1; st->alpha2 = a2; st->sigma_min = smin;
+    st->iter = 0;
+    st->done = 0;
+    st->converged = 0;
+    st->nonfinite = 0;
+    st->J_old = 0.0;
+    st->G = 0.0;
+    st->last_resid = 0.0;
+}
+
+__device__ double step_rule(const SolverState* st, double sigma, double gain, double G)
+{
+    if (gain < st->beta1 * sigma * G) {
+        const double s = st->alpha2 * sigma;
+        const double fl = fmin(st->sigma_min, sigma);
+        return fmax(s, fl);
+    }
+    if (gain > st->beta2 * sigma * G) return st->alpha1 * sigma;
+    return sigma;
+}
+
+// mode 0: J(phi_n) at the start of the phi-half (logged); 1: J(phi_{n+1/2});
+// mode 2: I(psi_{n+1/2}) at the start of the psi-half; 3: I(psi_{n+1}).
+__global__ void finalize_dual_kernel(SolverState* st, const double* pin, int nin,
+                                     const double* pout, int nout, double hd, int mode, Logs logs)
+{
+    if (st->done) return;
+    __shared__ double red[32];
+    const double a = block_sum_parts(pin, nin, red);
+    const double b = block_sum_parts(pout, nout, red);
+    if (threadIdx.x != 0) return;
+    const double J = hd * (a + b);
+    if (!isfinite(J)) { st->nonfinite = 1; st->done = 1; return; }
+    if (mode == 0) {
+        st->J_old = J;
+        if (logs.dual) logs.dual[st->iter] = J;
+        if (logs.sigma) logs.sigma[st->iter] = st->sigma;
+    } else if (mode == 2) {
+        st->J_old = J;
+    } else {
+        st->sigma = step_rule(st, st->sigma, J - st->J_old, st->G);
+        if (mode == 3) st->iter += 1;
+    }
+}
+
+// mode 0: phi-half G -> residual, convergence; 1: psi-half G; 2: Gref.
+__global__ void finalize_G_kernel(SolverState* st, const double* part, int np, int mode, Logs logs)
+{
+    if (mode != 2 && st->done) return;
+    __shared__ double red[32];
+    const double G = block_sum_parts(part, np, red);
+    if (threadIdx.x != 0) return;
+    if (!isfinite(G)) { st->nonfinite = 1; st->done = 1; return; }
+    if (mode == 2) { st->Gref = G; return; }
+    st->G = G;
+    if (mode == 0) {
+        const double r = st->Gref > 0.0 ? sqrt(fmax(G, 0.0) / st->Gref) : sqrt(fmax(G, 0.0));
+        st->last_resid = r;
+        if (logs.resid) logs.resid[st->iter] = r;
+        if (r < st->tol) { st->converged = 1; st->done = 1; }
+        else if (st->iter >= st->max_iter) st->done = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Workspace {
+    SolverState* state;
+    double* parts;            // kPartialSlots * kMaxPartials
+    double* logs;             // 3 * (max_iter + 1)
+    unsigned char* tables;    // per-axis tables
+    AxisTables tabs[3];
+    void* mu_n;
+    void* nu_n;
+    void* tmp;
+    void* rho;
+    size_t bytes;
+};
+
+static size_t tables_bytes(const Grid& g, int eb)
+{
+    size_t b = 0;
+    for (int a = 0; a < g.ndim; ++a) b += axis_table_bytes(g.n[a], eb);
+    return b;
+}
+
+static size_t poisson_bytes(const Grid& g, int eb)
+{
+    return up256(sizeof(SolverState)) + up256(sizeof(double) * kPartialSlots * kMaxPartials) +
+           tables_bytes(g, eb);
+}
+
+static size_t solve_bytes(const Grid& g, int eb, int max_iter)
+{
+    return poisson_bytes(g, eb) + up256(sizeof(double) * 3 * ((size_t)max_iter + 1)) +
+           4 * up256((size_t)eb * g.N);
+}
+
+static void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Workspace* w, bool fields)
+{
+    unsigned char* p = base;
+    w->state = reinterpret_cast<SolverState*>(p); p += up256(sizeof(SolverState));
+    w->parts = reinterpret_cast<double*>(p); p += up256(sizeof(double) * kPartialSlots * kMaxPartials);
+    w->tables = p;
+    for (int a = 0; a < g.ndim; ++a) {
+        w->tabs[a].tw = p;   // filled by fill_axis_tables
+        p += axis_table_bytes(g.n[a], eb);
+    }
+    if (fields) {
+        w->logs = reinterpret_cast<double*>(p); p += up256(sizeof(double) * 3 * ((size_t)max_iter + 1));
+        w->mu_n = p; p += up256((size_t)eb * g.N);
+        w->nu_n = p; p += up256((size_t)eb * g.N);
+        w->tmp = p;  p += up256((size_t)eb * g.N);
+        w->rho = p;  p += up256((size_t)eb * g.N);
+    } else {
+        w->logs = nullptr; w->mu_n = w->nu_n = w->tmp = w->rho = nullptr;
+    }
+    w->bytes = (size_t)(p - base);
+}
+
+template <typename T>
+static bfm_status fill_tables(const Grid& g, Workspace* w, cudaStream_t st)
+{
+    for (int a = 0; a < g.ndim; ++a) {
+        // axes of equal length still get their own copy: simple and tiny
+        bfm_status s = fill_axis_tables<T>(g.n[a], &w->tabs[a],
+                                           reinterpret_cast<unsigned char*>(w->tabs[a].tw), st);
+        if (s != BFM_OK) return s;
+    }
+    return BFM_OK;
+}
+
+static bool fft_sizes_ok(const Grid& g)
+{
+    FftRadices rs;
+    for (int a = 0; a < g.ndim; ++a)
+        if (!fft_radices(g.n[a], &rs)) return false;
+    return true;
+}
+
+static double* slot(Workspace* w, int s) { return w->parts + (size_t)s * kMaxPartials; }
+
+// ---------------------------------------------------------------------------
+// the pieces of one half step
+// ---------------------------------------------------------------------------
+// c-transform out = src^c with the two dot products of the dual value.
+template <typename T>
+static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_src, const T* w_out,
+                               double* p_in, int* n_in, double* p_out, int* n_out, const int* done,
+                               cudaStream_t st)
+{
+    for (int a = 0; a < g.ndim; ++a) {
+        const bool first = (a == 0), last = (a == g.ndim - 1);
+        int used = 0;
+        bfm_status s = launch_ct_pass<T>(g, a, first ? src : out, out, first,
+                                         first ? w_src : nullptr, first ? p_in : nullptr,
+                                         last ? w_out : nullptr, last ? p_out : nullptr, done,
+                                         kMaxPartials, st, &used);
+        if (s != BFM_OK) return s;
+        if (first) *n_in = used;
+        if (last) *n_out = used;
+    }
+    return BFM_OK;
+}
+
+// Forward transforms of f = base - in up to (and including) the middle pass;
+// the spectrum of g stays in `buf`.  G partials go to p_g.
+template <typename T>
+static bfm_status poisson_forward(const Grid& g, const AxisTables* tabs, const T* in,
+                                  const T* base, T* buf, double* p_g, int* n_g, const int* done,
+                                  cudaStream_t st)
+{
+    const int last = g.ndim - 1;
+    for (int a = 0; a < last; ++a) {
+        bfm_status s = launch_dct_pass<T>(g, a, PASS_FWD, tabs, a == 0 ? in : buf,
+                                          a == 0 ? base : nullptr, buf, nullptr, nullptr, nullptr,
+                                          done, st, nullptr);
+        if (s != BFM_OK) return s;
+    }
+    return launch_dct_pass<T>(g, last, PASS_MID, tabs, buf, nullptr, buf, nullptr, nullptr, p_g,
+                              done, st, n_g);
+}
+
+// Inverse transforms of the remaining axes; the last one writes
+// out = upd + sigma * g (or out = g when upd is NULL).
+template <typename T>
+static bfm_status poisson_inverse(const Grid& g, const AxisTables* tabs, T* buf, T* out,
+                                  const T* upd, const double* sigma, const int* done,
+                                  cudaStream_t st)
+{
+    for (int a = g.ndim - 2; a >= 0; --a) {
+        const bool final_ = (a == 0);
+        bfm_status s = launch_dct_pass<T>(g, a, PASS_INV, tabs, buf, nullptr, final_ ? out : buf,
+                                          final_ ? upd : nullptr, sigma, nullptr, done, st, nullptr);
+        if (s != BFM_OK) return s;
+    }
+    return BFM_OK;
+}
+
+template <typename T>
+static bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
+                            Logs logs, cudaStream_t st)
+{
+    const double hd = 1.0 / (double)g.N;
+    const int* done = &w->state->done;
+    T* mu = (T*)w->mu_n;
+    T* nu = (T*)w->nu_n;
+    T* tmp = (T*)w->tmp;
+    T* rho = (T*)w->rho;
+    // phi-half: src = phi (weight nu), transform weight mu, source measure mu, target nu
+    T* src = phi_half ? phi : psi;
+    T* dst = phi_half ? psi : phi;
+    const T* w_src = phi_half ? nu : mu;
+    const T* w_dst = phi_half ? mu : nu;
+    const T* source = phi_half ? mu : nu;
+    const T* target = phi_half ? nu : mu;
+    int ni = 0, no = 0, ng = 0;
+    bfm_status s;
+    s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st);
+    if (s != BFM_OK) return s;
+    finalize_dual_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+                                            phi_half ? 0 : 2, logs);
+    BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    s = launch_pushforward<T>(g, tmp, source, rho, done, st);
+    if (s != BFM_OK) return s;
+    s = poisson_forward<T>(g, w->tabs, rho, target, rho, slot(w, 2), &ng, done, st);
+    if (s != BFM_OK) return s;
+    finalize_G_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 2), ng, phi_half ? 0 : 1, logs);
+    BFM_LAUNCH_CHECK("finalize_G_kernel");
+    s = poisson_inverse<T>(g, w->tabs, rho, src, src, &w->state->sigma, done, st);
+    if (s != BFM_OK) return s;
+    s = ct_with_dots<T>(g, src, dst, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st);
+    if (s != BFM_OK) return s;
+    finalize_dual_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+                                            phi_half ? 1 : 3, logs);
+    BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    return BFM_OK;
+}
+
+template <typename T>
+static bfm_status measure_density(const Grid& g, const T* x, Workspace* w, int which, cudaStream_t st)
+{
+    const int th = 256;
+    long long nb = (g.N + th - 1) / th;
+    if (nb > 1024) nb = 1024;
+    stats_kernel<T><<<(int)nb, th, 0, st>>>(x, g.N, slot(w, 4), slot(w, 5), slot(w, 6), slot(w, 7));
+    BFM_LAUNCH_CHECK("stats_kernel");
+    stats_finalize_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 4), slot(w, 5), slot(w, 6),
+                                             slot(w, 7), (int)nb, 1.0 / (double)g.N, which);
+    BFM_LAUNCH_CHECK("stats_finalize_kernel");
+    return BFM_OK;
+}
+
+static int elem_bytes(bfm_precision p) { return p == BFM_FP64 ? 8 : 4; }
+
+template <typename T>
+static bfm_status solve_impl(const T* mu, const T* nu, const Grid& g, double tol, int max_iter,
+                             const bfm_options& o, unsigned char* wsp, cudaStream_t st,
+                             bfm_result* out)
+{
+    Workspace w;
+    carve(g, sizeof(T), max_iter, wsp, &w, true);
+    bfm_status s;
+    // -- input checks and normalisation -----------------------------------------
+    s = measure_density<T>(g, mu, &w, 0, st); if (s != BFM_OK) return s;
+    s = measure_density<T>(g, nu, &w, 1, st); if (s != BFM_OK) return s;
+    SolverState hs;
+    BFM_CUDA(cudaMemcpyAsync(&hs, w.state, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    BFM_CUDA(cudaStreamSynchronize(st));
+    if (hs.bad_mu || hs.bad_nu || hs.min_mu < 0.0 || hs.min_nu < 0.0 || !(hs.mass_mu > 0.0) ||
+        !(hs.mass_nu > 0.0)) {
+        set_last_error("densities must be finite, non-negative and of positive mass");
+        return BFM_ERR_INVALID_ARG;
+    }
+    const int th = 256;
+    int nb = (int)((g.N + th - 1) / th);
+    if (nb > num_sms() * 16) nb = num_sms() * 16;
+    scale_kernel<T><<<nb, th, 0, st>>>(mu, (T*)w.mu_n, g.N, w.state, 0);
+    scale_kernel<T><<<nb, th, 0, st>>>(nu, (T*)w.nu_n, g.N, w.state, 1);
+    BFM_LAUNCH_CHECK("scale_kernel");
+    init_state_kernel<<<1, 1, 0, st>>>(w.state, o.sigma0, tol, max_iter, o.beta1, o.beta2,
+                                       o.alpha1, o.alpha2, o.sigma_min);
+    BFM_LAUNCH_CHECK("init_state_kernel");
+    s = fill_tables<T>(g, &w, st); if (s != BFM_OK) return s;
+    // -- ||nu - 1||^2_{H^-1}: the mean of nu/mass is 1 and the zero mode is dropped
+    int ng = 0;
+    s = poisson_forward<T>(g, w.tabs, (const T*)w.nu_n, nullptr, (T*)w.rho, slot(&w, 2), &ng,
+                           nullptr, st);
+    if (s != BFM_OK) return s;
+    Logs logs;
+    const int L = max_iter + 1;
+    logs.dual = w.logs;
+    logs.resid = w.logs + L;
+    logs.sigma = w.logs + 2 * L;
+    finalize_G_kernel<<<1, 256, 0, st>>>(w.state, slot(&w, 2), ng, 2, logs);
+    BFM_LAUNCH_CHECK("finalize_G_kernel");
+    T* phi = (T*)out->phi;
+    T* psi = (T*)out->psi;
+    if (!o.warm_start) BFM_CUDA(cudaMemsetAsync(phi, 0, sizeof(T) * g.N, st));
+    BFM_CUDA(cudaMemsetAsync(psi, 0, sizeof(T) * g.N, st));
+    BFM_CUDA(cudaMemsetAsync(w.logs, 0, sizeof(double) * 3 * L, st));
+    // -- iterations --------------------------------------------------------------------
+    const int poll = o.poll_every > 0 ? o.poll_every : 4;
+    int enq = 0;
+    while (enq <= max_iter) {
+        const int chunk = (max_iter + 1 - enq) < poll ? (max_iter + 1 - enq) : poll;
+        for (int c = 0; c < chunk; ++c) {
+            s = half_step<T>(g, &w, true, phi, psi, logs, st); if (s != BFM_OK) return s;
+            s = half_step<T>(g, &w, false, phi, psi, logs, st); if (s != BFM_OK) return s;
+        }
+        enq += chunk;
+        int done = 0;
+        BFM_CUDA(cudaMemcpyAsync(&done, &w.state->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BFM_CUDA(cudaStreamSynchronize(st));
+        if (done) break;
+    }
+    BFM_CUDA(cudaMemcpyAsync(&hs, w.state, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    BFM_CUDA(cudaStreamSynchronize(st));
+    if (hs.nonfinite) {
+        set_last_error("a reduction produced a non-finite value");
+        return BFM_ERR_NONFINITE;
+    }
+    // -- outputs: phi_n, psi = phi_n^c (left in tmp by the last phi-half), the map
+    BFM_CUDA(cudaMemcpyAsync(psi, w.tmp, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, st));
+    if (out->map) { s = launch_map<T>(g, psi, (T*)out->map, st); if (s != BFM_OK) return s; }
+    const int nlog = hs.iter + 1;
+    if (out->dual) BFM_CUDA(cudaMemcpyAsync(out->dual, logs.dual, sizeof(double) * nlog, cudaMemcpyDeviceToHost, st));
+    if (out->resid) BFM_CUDA(cudaMemcpyAsync(out->resid, logs.resid, sizeof(double) * nlog, cudaMemcpyDeviceToHost, st));
+    if (out->sigma) BFM_CUDA(cudaMemcpyAsync(out->sigma, logs.sigma, sizeof(double) * nlog, cudaMemcpyDeviceToHost, st));
+    BFM_CUDA(cudaStreamSynchronize(st));
+    out->w2sq = 2.0 * hs.J_old;
+    out->mass_mu = hs.mass_mu;
+    out->mass_nu = hs.mass_nu;
+    out->max_mu = hs.max_mu;
+    out->max_nu = hs.max_nu;
+    out->sigma_final = hs.sigma;
+    out->iters = hs.iter;
+    out->converged = hs.converged;
+    return hs.converged ? BFM_OK : BFM_NOT_CONVERGED;
+}
+
+}  // namespace bfm
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace bfm;
+
+static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
+extern "C" size_t bfm_workspace_bytes(const bfm_grid* grid, bfm_precision prec, int max_iter)
+{
+    Grid g;
+    if (!make_grid(grid, &g) || max_iter < 0) return 0;
+    return solve_bytes(g, elem_bytes(prec), max_iter);
+}
+
+extern "C" size_t bfm_workspace_bytes_host(const bfm_grid* grid, bfm_precision prec, int max_iter)
+{
+    Grid g;
+    if (!make_grid(grid, &g) || max_iter < 0) return 0;
+    const size_t f = up256((size_t)elem_bytes(prec) * g.N);
+    return solve_bytes(g, elem_bytes(prec), max_iter) + 4 * f + up256((size_t)elem_bytes(prec) * g.N * g.ndim);
+}
+
+extern "C" size_t bfm_poisson_workspace_bytes(const bfm_grid* grid, bfm_precision prec)
+{
+    Grid g;
+    if (!make_grid(grid, &g)) return 0;
+    return poisson_bytes(g, elem_bytes(prec));
+}
+
+static bfm_status check_common(const bfm_grid* grid, bfm_precision prec, Grid* g)
+{
+    if (prec != BFM_FP32 && prec != BFM_FP64) return BFM_ERR_INVALID_ARG;
+    if (!make_grid(grid, g)) {
+        set_last_error("grid must have ndim 2 or 3 and 2 <= n <= 8192 per axis");
+        return BFM_ERR_INVALID_ARG;
+    }
+    return BFM_OK;
+}
+
+extern "C" bfm_status bfm_solve(const void* mu, const void* nu, const bfm_grid* grid, bfm_cost cost,
+                                bfm_precision prec, double tol, int max_iter, const bfm_options* opt,
+                                void* workspace, size_t workspace_bytes, void* stream,
+                                bfm_result* out)
+{
+    Grid g;
+    bfm_status s = check_common(grid, prec, &g);
+    if (s != BFM_OK) return s;
+    if (cost != BFM_COST_QUADRATIC) { set_last_error("only the quadratic cost is implemented"); return BFM_ERR_UNSUPPORTED; }
+    if (!fft_sizes_ok(g)) { set_last_error("every n[a] must be 2^p 3^q"); return BFM_ERR_UNSUPPORTED; }
+    if (!mu || !nu || !out || !out->phi || !out->psi || !(tol >= 0.0) || max_iter < 0 ||
+        max_iter > 10000000) {
+        set_last_error("null pointer, negative tolerance or bad max_iter");
+        return BFM_ERR_INVALID_ARG;
+    }
+    if (!workspace || !aligned256(workspace) ||
+        workspace_bytes < solve_bytes(g, elem_bytes(prec), max_iter)) {
+        set_last_error("workspace NULL, not 256-byte aligned or smaller than bfm_workspace_bytes()");
+        return BFM_ERR_WORKSPACE;
+    }
+    bfm_options o;
+    bfm_default_options(&o);
+    if (opt) o = *opt;
+    if (!(o.beta1 > 0 && o.beta1 < o.beta2 && o.beta2 < 1 && o.alpha1 > 1 && o.alpha2 > 0 &&
+          o.alpha2 < 1 && o.sigma_min >= 0)) {
+        set_last_error("step rule needs 0 < beta1 < beta2 < 1, alpha1 > 1, 0 < alpha2 < 1");
+        return BFM_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* wsp = (unsigned char*)workspace;
+    if (prec == BFM_FP32)
+        return solve_impl<float>((const float*)mu, (const float*)nu, g, tol, max_iter, o, wsp, st, out);
+    return solve_impl<double>((const double*)mu, (const double*)nu, g, tol, max_iter, o, wsp, st, out);
+}
+
+extern "C" bfm_status bfm_solve_host(const void* mu, const void* nu, const bfm_grid* grid,
+                                     bfm_cost cost, bfm_precision prec, double tol, int max_iter,
+                                     const bfm_options* opt, void* workspace, size_t workspace_bytes,
+                                     void* stream, bfm_result* out)
+{
+    Grid g;
+    bfm_status s = check_common(grid, prec, &g);
+    if (s != BFM_OK) return s;
+    if (!mu || !nu || !out || !out->phi || !out->psi || max_iter < 0) return BFM_ERR_INVALID_ARG;
+    const size_t need = bfm_workspace_bytes_host(grid, prec, max_iter);
+    if (!workspace || !aligned256(workspace) || workspace_bytes < need) return BFM_ERR_WORKSPACE;
+    const int eb = elem_bytes(prec);
+    const size_t fb = (size_t)eb * g.N;
+    const size_t f = up256(fb);
+    unsigned char* p = (unsigned char*)workspace + solve_bytes(g, eb, max_iter);
+    void* dmu = p; void* dnu = p + f; void* dphi = p + 2 * f; void* dpsi = p + 3 * f;
+    void* dmap = p + 4 * f;
+    cudaStream_t st = (cudaStream_t)stream;
+    BFM_CUDA(cudaMemcpyAsync(dmu, mu, fb, cudaMemcpyHostToDevice, st));
+    BFM_CUDA(cudaMemcpyAsync(dnu, nu, fb, cudaMemcpyHostToDevice, st));
+    bfm_result r = *out;
+    r.phi = dphi; r.psi = dpsi; r.map = out->map ? dmap : nullptr;
+    if (opt && opt->warm_start) BFM_CUDA(cudaMemcpyAsync(dphi, out->phi, fb, cudaMemcpyHostToDevice, st));
+    s = bfm_solve(dmu, dnu, grid, cost, prec, tol, max_iter, opt, workspace,
+                  solve_bytes(g, eb, max_iter), stream, &r);
+    if (s < 0) return s;
+    BFM_CUDA(cudaMemcpyAsync(out->phi, dphi, fb, cudaMemcpyDeviceToHost, st));
+    BFM_CUDA(cudaMemcpyAsync(out->psi, dpsi, fb, cudaMemcpyDeviceToHost, st));
+    if (out->map) BFM_CUDA(cudaMemcpyAsync(out->map, dmap, fb * g.ndim, cudaMemcpyDeviceToHost, st));
+    BFM_CUDA(cudaStreamSynchronize(st));
+    void* keep_phi = out->phi; void* keep_psi = out->psi; void* keep_map = out->map;
+    *out = r;
+    out->phi = keep_phi; out->psi = keep_psi; out->map = keep_map;
+    return s;
+}
+
+extern "C" bfm_status bfm_ctransform(const void* phi, void* out, const bfm_grid* grid,
+                                     bfm_precision prec, void* stream)
+{
+    Grid g;
+    bfm_status s = check_common(grid, prec, &g);
+    if (s != BFM_OK) return s;
+    if (!phi || !out) return BFM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int a = 0; a < g.ndim; ++a) {
+        if (prec == BFM_FP32)
+            s = launch_ct_pass<float>(g, a, a == 0 ? (const float*)phi : (const float*)out, (float*)out,
+                                      a == 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0, st, nullptr);
+        else
+            s = launch_ct_pass<double>(g, a, a == 0 ? (const double*)phi : (const double*)out,
+                                       (double*)out, a == 0, nullptr, nullptr, nullptr, nullptr,
+                                       nullptr, 0, st, nullptr);
+        if (s != BFM_OK) return s;
+    }
+    BFM_LAUNCH_CHECK("ct_pass_kernel");
+    return BFM_OK;
+}
+
+template <typename T>
+static bfm_status poisson_impl(const T* f, T* gout, const Grid& g, double* G_out,
+                               unsigned char* wsp, cudaStream_t st)
+{
+    Workspace w;
+    carve(g, sizeof(T), 0, wsp, &w, false);
+    bfm_status s = fill_tables<T>(g, &w, st);
+    if (s != BFM_OK) return s;
+    int ng = 0;
+    s = poisson_forward<T>(g, w.tabs, f, nullptr, gout, slot(&w, 2), &ng, nullptr, st);
+    if (s != BFM_OK) return s;
+    s = poisson_inverse<T>(g, w.tabs, gout, gout, nullptr, nullptr, nullptr, st);
+    if (s != BFM_OK) return s;
+    if (G_out) {
+        Logs none = {nullptr, nullptr, nullptr};
+        finalize_G_kernel<<<1, 256, 0, st>>>(w.state, slot(&w, 2), ng, 2, none);
+        BFM_LAUNCH_CHECK("finalize_G_kernel");
+        BFM_CUDA(cudaMemcpyAsync(G_out, &w.state->Gref, sizeof(double), cudaMemcpyDeviceToHost, st));
+        BFM_CUDA(cudaStreamSynchronize(st));
+    }
+    return BFM_OK;
+}
+
+extern "C" bfm_status bfm_poisson(const void* f, void* g_out, const bfm_grid* grid,
+                                  bfm_precision prec, double* G_out, void* workspace,
+                                  size_t workspace_bytes, void* stream)
+{
+    Grid g;
+    bfm_status s = check_common(grid, prec, &g);
+    if (s != BFM_OK) return s;
+    if (!fft_sizes_ok(g)) { set_last_error("every n[a] must be 2^p 3^q"); return BFM_ERR_UNSUPPORTED; }
+    if (!f || !g_out) return BFM_ERR_INVALID_ARG;
+    if (!workspace || !aligned256(workspace) || workspace_bytes < poisson_bytes(g, elem_bytes(prec)))
+        return BFM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == BFM_FP32)
+        return poisson_impl<float>((const float*)f, (float*)g_out, g, G_out, (unsigned char*)workspace, st);
+    return poisson_impl<double>((const double*)f, (double*)g_out, g, G_out, (unsigned char*)workspace, st);
+}
+
+extern "C" bfm_status bfm_map(const void* psi, void* map, const bfm_grid* grid, bfm_precision prec,
+                              void* stream)
+{
+    Grid g;
+    bfm_status s = check_common(grid, prec, &g);
+    if (s != BFM_OK) return s;
+    if (!psi || !map) return BFM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == BFM_FP32) return launch_map<float>(g, (const float*)psi, (float*)map, st);
+    return launch_map<double>(g, (const double*)psi, (double*)map, st);
+}
+
+extern "C" bfm_status bfm_pushforward(const void* psi, const void* mu, void* rho,
+                                      const bfm_grid* grid, bfm_precision prec, void* stream)
+{
+    Grid g;
+    bfm_status s = check_common(grid, prec, &g);
+    if (s != BFM_OK) return s;
+    if (!psi || !mu || !rho) return BFM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == BFM_FP32)
+        return launch_pushforward<float>(g, (const float*)psi, (const float*)mu, (float*)rho, nullptr, st);
+    return launch_pushforward<double>(g, (const double*)psi, (const double*)mu, (double*)rho, nullptr, st);
+}
+
+extern "C" bfm_status bfm_interpolate(const void* map, const void* mu, double t, void* rho,
+                                      const bfm_grid* grid, bfm_precision prec, void* stream)
+{
+    Grid g;
+    bfm_status s = check_common(grid, prec, &g);
+    if (s != BFM_OK) return s;
+    if (!map || !mu || !rho || !(t >= 0.0 && t <= 1.0)) return BFM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == BFM_FP32)
+        return launch_interpolate<float>(g, (const float*)map, (const float*)mu, t, (float*)rho, st);
+    return launch_interpolate<double>(g, (const double*)map, (const double*)mu, t, (double*)rho, st);
+}

@@ -1,0 +1,227 @@
+"""Parity of the CUDA path with the FP64 oracle, step by step (marked gpu).
+
+Each test runs a C-ABI entry point of libbfm.so through the thin binding and
+compares it element by element with the oracle on the same seeded inputs, at
+sizes that span several line tiles and leave ragged tails (line counts that
+are not multiples of the tile width, line lengths that are not multiples of
+the per-thread chunk).
+
+Tolerances:
+  FP64  c-transform / map / pushforward: 1e-12 relative to the field scale (a
+        minimum over identical candidates can differ only by rounding);
+        Poisson 1e-10 (FFT vs definition order of summation).
+  FP32  the oracle is run on the FP32 input widened to FP64, so the only
+        differences are FP32 rounding in the kernels: c-transform 4 ulp of
+        the field scale, Poisson 2e-5 relative, pushforward 2e-5 of max rho.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1905_12154_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def dev(x, dt=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+CT_SHAPES = [(2, 2), (7, 5), (64, 64), (33, 100), (257, 96), (48, 31, 20), (9, 40, 13)]
+
+
+@pytest.mark.parametrize("shape", CT_SHAPES, ids=str)
+def test_ctransform_fp64(B, shape):
+    for seed, phi in ((1, si.random_field(shape, 1, 0.1)),
+                      (2, si.smooth_potential(tuple(reversed(shape)), 2, 0.2))):
+        want = oracle.ctransform(phi, "brute" if phi.size <= 70000 else "linear")
+        got = host(B.bfm_ctransform(dev(phi)))
+        scale = 1.0 + np.max(np.abs(phi))
+        assert np.max(np.abs(got - want)) <= 1e-12 * scale, (shape, seed)
+
+
+@pytest.mark.parametrize("shape", CT_SHAPES, ids=str)
+def test_ctransform_fp32(B, shape):
+    phi = si.smooth_potential(tuple(reversed(shape)), 3, 0.2) + 0.01 * si.random_field(shape, 3)
+    phi32 = phi.astype(np.float32)
+    want = oracle.ctransform(phi32.astype(np.float64), "linear")
+    got = host(B.bfm_ctransform(dev(phi32, torch.float32)))
+    scale = 1.0 + np.max(np.abs(phi))
+    assert np.max(np.abs(got - want)) <= 4 * np.finfo(np.float32).eps * scale
+
+
+def test_ctransform_in_place_and_invariants(B):
+    phi = dev(si.random_field((40, 56), 4, 0.1))
+    c1 = B.bfm_ctransform(phi)
+    c2 = B.bfm_ctransform(c1)
+    c3 = B.bfm_ctransform(c2)
+    assert torch.all(phi <= c2 + 1e-15)            # Lemma 2.2(i)
+    assert torch.max(torch.abs(c3 - c1)).item() < 1e-14
+    x = c1.clone()
+    B.bfm_ctransform(x, out=x)                      # in place
+    assert torch.equal(x, c2)
+
+
+POISSON_SHAPES = [(2, 3), (16, 12), (64, 48), (96, 128), (27, 32), (384, 8), (12, 18, 16),
+                  (24, 6, 9)]
+
+
+@pytest.mark.parametrize("shape", POISSON_SHAPES, ids=str)
+def test_poisson_fp64(B, shape):
+    f = si.random_field(shape, 5)
+    g_want, G_want = oracle.poisson(f, "definition" if f.size <= 5000 else "fft")
+    g_got, G_got = B.bfm_poisson(dev(f))
+    g_got = host(g_got)
+    scale = np.max(np.abs(g_want))
+    assert np.max(np.abs(g_got - g_want)) <= 1e-10 * scale
+    assert abs(G_got - G_want) <= 1e-10 * abs(G_want)
+
+
+@pytest.mark.parametrize("shape", [(64, 48), (256, 96), (12, 18, 16)], ids=str)
+def test_poisson_fp32(B, shape):
+    f = si.random_field(shape, 6).astype(np.float32)
+    g_want, G_want = oracle.poisson(f.astype(np.float64))
+    g_got, G_got = B.bfm_poisson(dev(f, torch.float32))
+    g_got = host(g_got)
+    assert np.max(np.abs(g_got - g_want)) <= 2e-5 * np.max(np.abs(g_want))
+    assert abs(G_got - G_want) <= 2e-5 * abs(G_want)
+
+
+def test_poisson_unsupported_size(B):
+    with pytest.raises(B.BfmError) as e:
+        B.bfm_poisson(dev(np.zeros((7, 8))))
+    assert e.value.status == B.BFM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (37, 50), (20, 18, 22)], ids=str)
+def test_map_and_pushforward_fp64(B, shape):
+    mu = si.normalise(np.abs(si.random_field(shape, 7)) * (si.random_field(shape, 8) > -0.5))
+    psi = si.smooth_potential(tuple(reversed(shape)), 9, 0.1)
+    tmap = host(B.bfm_map(dev(psi)))
+    assert np.max(np.abs(tmap - oracle.transport_map(psi))) <= 1e-13
+    rho = host(B.bfm_pushforward(dev(psi), dev(mu)))
+    want = oracle.pushforward(psi, mu)
+    assert np.max(np.abs(rho - want)) <= 1e-12 * np.max(want)
+    assert abs(rho.sum() - mu.sum()) <= 1e-12 * mu.sum()
+
+
+def test_pushforward_fp32(B):
+    shape = (128, 96)
+    mu = si.normalise(np.abs(si.random_field(shape, 10))).astype(np.float32)
+    psi = si.smooth_potential((96, 128), 11, 0.1).astype(np.float32)
+    rho = host(B.bfm_pushforward(dev(psi, torch.float32), dev(mu, torch.float32)))
+    want = oracle.pushforward(psi.astype(np.float64), mu.astype(np.float64))
+    assert np.max(np.abs(rho - want)) <= 2e-5 * np.max(want)
+
+
+def test_interpolate(B):
+    n = 64
+    mu, nu = si.translated_discs(n)
+    x, y = si.centres((n, n))
+    T = np.stack([np.minimum(x + 0.5, 1 - 0.5 / n), np.minimum(y + 0.5, 1 - 0.5 / n)])
+    for t in (0.0, 0.3, 0.5, 1.0):
+        got = host(B.bfm_interpolate(dev(T), dev(mu), t))
+        assert np.max(np.abs(got - oracle.interpolate(T, mu, t))) <= 1e-12 * np.max(mu)
+
+
+# --- the whole method ---------------------------------------------------------
+
+def test_solve_translated_discs_fp64(B):
+    """Table 1 case: GPU and oracle follow the same iterates to rounding."""
+    mu, nu = si.translated_discs(64)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=8)
+    r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=8)
+    assert r["iters"] == ref["iters"] == 8
+    assert np.max(np.abs(r["dual"] - ref["dual"])) < 1e-12
+    assert np.max(np.abs(r["resid"] - ref["resid"])) < 1e-9
+    assert np.max(np.abs(r["sigma"] - ref["sigma"])) < 1e-12
+    assert abs(r["w2sq"] - 0.5) < 1e-12
+    assert np.max(np.abs(host(r["phi"]) - ref["phi"])) < 1e-10
+    assert np.max(np.abs(host(r["psi"]) - ref["psi"])) < 1e-10
+    assert np.max(np.abs(host(r["map"]) - ref["map"])) * 64 < 1e-8     # in cells
+
+
+def test_solve_gauss_disc_64_fp64(B):
+    """3 Gaussians -> disc, 64x64, FP64 plain method, tol 1e-6 or 300 iterations."""
+    mu, nu = si.workload_gauss_disc_64()
+    ref = oracle.solve(mu, nu, tol=1e-6, max_iter=300)
+    r = B.bfm_solve(dev(mu), dev(nu), tol=1e-6, max_iter=300)
+    assert r["iters"] == ref["iters"]
+    assert r["converged"] == ref["converged"]
+    k = min(len(r["dual"]), len(ref["dual"]))
+    assert np.max(np.abs(r["dual"][:k] - ref["dual"][:k])) < 1e-9
+    assert np.max(np.abs(r["resid"][:k] - ref["resid"][:k])) < 1e-6
+    assert abs(r["w2sq"] - ref["w2sq"]) / ref["w2sq"] < 1e-9
+    assert np.max(np.abs(host(r["map"]) - ref["map"])) * 64 < 1e-4      # in cells
+
+
+def test_solve_3d_fp64(B):
+    mu, nu = si.translated_balls(24)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=6)
+    r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=6)
+    assert np.max(np.abs(r["dual"] - ref["dual"])) < 1e-11
+    assert abs(r["w2sq"] - ref["w2sq"]) < 1e-11
+
+
+def test_solve_fp32_matches_fp64_oracle(B):
+    """FP32 bulk with FP64 reductions: W2^2 within 1e-5 relative of the oracle."""
+    mu, nu = si.workload_annulus_5g_4096(256)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=30)
+    r = B.bfm_solve(dev(mu, torch.float32), dev(nu, torch.float32), tol=0.0, max_iter=30)
+    assert r["iters"] == 30
+    assert abs(r["w2sq"] - ref["w2sq"]) / ref["w2sq"] < 1e-5
+    assert np.max(np.abs(r["resid"] - ref["resid"])) < 1e-3
+    assert np.max(np.abs(host(r["map"]) - ref["map"])) * 256 < 0.05     # in cells
+
+
+def test_solve_host_buffers(B):
+    mu, nu = si.translated_discs(32)
+    r = B.bfm_solve_host(mu, nu, tol=0.0, max_iter=5)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=5)
+    assert abs(r["w2sq"] - ref["w2sq"]) < 1e-12
+    assert np.max(np.abs(r["phi"] - ref["phi"])) < 1e-10
+
+
+def test_solve_converges_and_stops(B):
+    mu, nu = si.translated_discs(64)
+    r = B.bfm_solve(dev(mu), dev(nu), tol=1e-2, max_iter=50)
+    ref = oracle.solve(mu, nu, tol=1e-2, max_iter=50)
+    assert r["converged"] and r["status"] == B.BFM_OK
+    assert r["iters"] == ref["iters"] < 50
+    assert r["resid"][-1] < 1e-2
+
+
+def test_solve_rejects_bad_input(B):
+    mu, nu = si.translated_discs(16)
+    for bad in (-mu, np.zeros_like(mu), np.where(mu > 0, np.nan, 0.0)):
+        with pytest.raises(B.BfmError) as e:
+            B.bfm_solve(dev(bad), dev(nu), max_iter=2)
+        assert e.value.status == B.BFM_ERR_INVALID_ARG
+    with pytest.raises(B.BfmError) as e:
+        B.bfm_solve(dev(np.ones((5, 7))), dev(np.ones((5, 7))), max_iter=2)
+    assert e.value.status == B.BFM_ERR_UNSUPPORTED
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.BfmError) as e:
+        B.bfm_solve(dev(mu), dev(nu), max_iter=2, workspace=ws)
+    assert e.value.status == B.BFM_ERR_WORKSPACE
+
+
+def test_solve_max_iter_zero(B):
+    mu, nu = si.translated_discs(16)
+    r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=0)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=0)
+    assert r["iters"] == 0 and r["status"] == B.BFM_NOT_CONVERGED
+    assert abs(r["resid"][0] - ref["resid"][0]) < 1e-12
