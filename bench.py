@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the back-and-forth method on one GB300 (or N replicas).
+
+Workload: the 4096x4096 2D problem, mu = uniform annulus (radii 0.15-0.35,
+centre (0.3, 0.5)), nu = 5 seeded Gaussians truncated below 1e-3 max, FP32
+fields with FP64 reductions.  A step is one back-and-forth iteration (both
+half steps: 4 c-transforms, 2 pushforwards, 2 Poisson solves, the step rule).
+The JSON line reports iterations/s over K timed steps (CUDA events on the
+solver's stream, inputs resident in HBM, working set of six 64 MiB fields,
+larger than L2), plus: the time and iterations to reach relative residual
+1e-3 from scratch in FP32 and in the plain FP64 mode on the same GPU; the
+same solve end to end through the host-buffer C-ABI call; the roofline of
+the dominant kernel; clocks sampled during the timed region; and the FP64
+CPU oracle timed on the host cores.
+
+--impl reference times the FP64 CPU oracle on the same workload instead.
+Under torchrun each rank solves its own copy of the problem (replicas: the
+single-problem path has no exchange to shard), value = all ranks' steps /
+max elapsed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFM iterations/s (4096^2 FP32, FP64 reductions)"
+UNIT = "iter/s"
+
+# algorithmic bytes per grid cell of one launch, FP32 fields (each input read
+# and each output written once); see DESIGN.md "Algorithmic bytes"
+BYTES_PER_CELL_2D = {
+    "ct_pass_axis0": 12,   # read phi, read weight (dual dot), write
+    "ct_pass_axis1": 12,   # read, write, read weight (dual dot)
+    "dct_fwd": 12,         # read rho, read target density, write
+    "dct_mid": 8,          # read, write
+    "dct_inv": 12,         # read spectrum, read potential, write potential
+    "pushforward": 16,     # zero rho, read psi, read mu, write rho
+}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "-i", str(self.idx),
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1])); smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_iteration_seconds(mu, nu, iters: int) -> tuple[float, int]:
+    """Seconds per oracle iteration: t(iters) - t(0), over `iters` iterations."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.solve(mu, nu, tol=0.0, max_iter=0)
+    t1 = time.perf_counter()
+    oracle.solve(mu, nu, tol=0.0, max_iter=iters)
+    t2 = time.perf_counter()
+    return max((t2 - t1) - (t1 - t0), 1e-9) / iters, oracle.threads()
+
+
+def run_reference(args, ws, rank):
+    """The FP64 CPU oracle on the same workload, one iteration per step."""
+    if rank != 0:
+        return
+    import synthetic_inputs as si
+    import oracle
+    oracle.build()
+    mu, nu = si.workload_annulus_5g_4096(args.n)
+    # one oracle iteration at 4096^2 takes seconds; time as many of the
+    # requested steps as fit in the budget (at least one), no warm-up needed
+    budget = args.reference_budget_s
+    probe, cores = oracle_iteration_seconds(mu, nu, 1)
+    k = max(1, min(args.steps, int(budget / max(probe, 1e-6)) - 1))
+    per_it = probe if k == 1 else oracle_iteration_seconds(mu, nu, k)[0]
+    value = 1.0 / per_it
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": k, "requested_steps": args.steps, "warmup": 0, "ms_per_step": per_it * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.n),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{k} oracle iteration(s) of the {args.n}^2 workload "
+                                   "(Legendre-line c-transform, FFT DCT), setup excluded"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(n):
+    return {"workload": f"annulus -> 5 truncated Gaussians, {n}x{n} cell-centred grid",
+            "grid": [n, n], "fields": "FP32", "reductions": "FP64",
+            "step": "one back-and-forth iteration (4 c-transforms, 2 pushforwards, 2 Poisson solves)",
+            "l2": "inputs larger than L2 (6 resident fields of 64 MiB each)", "tol": 1e-3}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--no-extras", action="store_true", help="only the timed steps")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-budget-s", type=float, default=150.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import numpy as np
+    import torch
+    import synthetic_inputs as si
+    from paper_1905_12154_gb300 import binding as B
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    mu_h, nu_h = si.workload_annulus_5g_4096(args.n)
+    mu = torch.from_numpy(mu_h).to(dev, torch.float32)
+    nu = torch.from_numpy(nu_h).to(dev, torch.float32)
+    N = mu.numel()
+    stream = torch.cuda.current_stream()
+
+    # ---- timed steps ---------------------------------------------------------------
+    solver = B.BfmSolver(mu, nu, tol=0.0, max_iter=args.warmup + args.steps + 2)
+    solver.iterate(args.warmup)
+    torch.cuda.synchronize()
+    clock = ClockSampler(dev.index if dev.index is not None else 0)
+    clock.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    B.bfm_profile_begin(args.steps * 40 + 64)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    prof = B.bfm_profile_end()
+    clocks = clock.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if pg:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = ws * args.steps / elapsed
+    res_timed = solver.finish(with_map=False)
+
+    # ---- roofline of the dominant kernel (live CUDA-event times) ---------------------------
+    pk, src = peaks()
+    kinds = {k: v for k, v in prof.items() if not k.startswith("_")}
+    launches = sum(c for _, c in kinds.values())
+    dom = max((k for k in kinds if k in BYTES_PER_CELL_2D), key=lambda k: kinds[k][0])
+    ms, cnt = kinds[dom]
+    bytes_per_launch = BYTES_PER_CELL_2D[dom] * N
+    achieved = bytes_per_launch / (ms / cnt / 1e3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+            "bytes_per_launch": bytes_per_launch, "avg_launch_ms": ms / cnt}
+    total_alg = sum(BYTES_PER_CELL_2D.get(k, 0) * N * c for k, (m, c) in kinds.items())
+    per_iter = {"alg_bytes_per_iter": total_alg / args.steps,
+                "hbm_frac_per_iter": (total_alg / elapsed * ws / ws) / 1e9 / pk["hbm_gbs"] if ws == 1 else None}
+    breakdown = {k: {"ms_per_iter": m / args.steps, "launches_per_iter": c / args.steps,
+                     "share": m / max(sum(x for x, _ in kinds.values()), 1e-12)}
+                 for k, (m, c) in kinds.items() if c}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args.n), "gpu_launches": launches, "clocks": clocks,
+        "roofline": roof, "per_iteration": per_iter, "breakdown": breakdown,
+        "max_density_ratio": {"max_mu": res_timed["max_mu"], "max_nu": res_timed["max_nu"],
+                              "max": max(res_timed["max_mu"], res_timed["max_nu"]),
+                              "nu_over_mu": res_timed["max_nu"] / res_timed["max_mu"]},
+    }
+
+    if rank == 0 and not args.no_extras:
+        # ---- time to tol from scratch, FP32 and plain FP64 on the same GPU --------------
+        def to_tol(dtype):
+            m = torch.from_numpy(mu_h).to(dev, dtype)
+            n_ = torch.from_numpy(nu_h).to(dev, dtype)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = B.bfm_solve(m, n_, tol=args.tol, max_iter=2000, with_map=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return r, a.elapsed_time(b) / 1e3
+        r32, t32 = to_tol(torch.float32)
+        r64, t64 = to_tol(torch.float64)
+        line["time_to_tol"] = {
+            "tol": args.tol,
+            "fp32": {"seconds": t32, "iters": r32["iters"], "converged": r32["converged"],
+                     "w2sq": r32["w2sq"], "final_resid": float(r32["resid"][-1])},
+            "fp64": {"seconds": t64, "iters": r64["iters"], "converged": r64["converged"],
+                     "w2sq": r64["w2sq"], "final_resid": float(r64["resid"][-1])},
+            "fp32_vs_fp64": {"rel_dw2sq": abs(r32["w2sq"] - r64["w2sq"]) / r64["w2sq"],
+                             "map_linf_cells": float(torch.max(torch.abs(
+                                 r32["map"].double() - r64["map"])).item() * args.n)},
+        }
+        # plain FP64 iterations/s on the same GPU
+        s64 = B.BfmSolver(torch.from_numpy(mu_h).to(dev), torch.from_numpy(nu_h).to(dev),
+                          tol=0.0, max_iter=60)
+        s64.iterate(3)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record(stream); s64.iterate(40); b.record(stream)
+        torch.cuda.synchronize()
+        line["fp64_iters_per_s"] = 40 / (a.elapsed_time(b) / 1e3)
+        del s64
+        # ---- end to end through the host-buffer C-ABI call ---------------------------------
+        mu_p = torch.from_numpy(mu_h.astype(np.float32)).pin_memory()
+        nu_p = torch.from_numpy(nu_h.astype(np.float32)).pin_memory()
+        t0 = time.perf_counter()
+        re = B.bfm_solve_host(mu_p.numpy(), nu_p.numpy(), tol=args.tol, max_iter=2000,
+                              with_map=True)
+        te = time.perf_counter() - t0
+        h2d = 2 * N * 4
+        d2h = (2 + 2) * N * 4 + 3 * 8 * (re["iters"] + 1)
+        line["e2e"] = {"value": re["iters"] / te, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d / max(re["iters"], 1),
+                       "d2h_bytes_per_step": d2h / max(re["iters"], 1),
+                       "seconds_per_solve": te, "iters_per_solve": re["iters"],
+                       "h2d_bytes_per_solve": h2d, "d2h_bytes_per_solve": d2h,
+                       "call": "bfm_solve_host (pinned host mu, nu -> phi, psi, map), tol 1e-3"}
+        # ---- the FP64 CPU oracle on the host cores ----------------------------------------
+        if ws == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            sec, cores = oracle_iteration_seconds(mu_h, nu_h, 1)
+            line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": cores,
+                                    "kind": "oracle",
+                                    "sample": f"1 oracle iteration of the {args.n}^2 workload "
+                                              "(FP64, Legendre-line c-transform, FFT DCT), "
+                                              "timed as t(1 iteration) - t(setup only)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

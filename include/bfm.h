@@ -131,6 +131,49 @@ bfm_status bfm_solve(const void *mu, const void *nu, const bfm_grid *grid, bfm_c
                      bfm_precision prec, double tol, int max_iter, const bfm_options *opt,
                      void *workspace, size_t workspace_bytes, void *stream, bfm_result *out);
 
+/*
+ * The same solve driven step by step by the caller (Algorithm 1 as above);
+ * all solver state lives in the workspace and the host keeps nothing between
+ * calls.  Each call takes the same grid, precision, max_iter and workspace.
+ *   bfm_solver_init     validates and normalises mu, nu (DEVICE, N each), fills
+ *                       the tables, measures ||nu - 1||^2_{H^-1} and sets
+ *                       phi_0 = 0 (or keeps phi when opt->warm_start) in `phi`;
+ *                       `phi`, `psi` are DEVICE fields of N elements that hold
+ *                       the iterates.  Synchronises once to check the inputs.
+ *   bfm_solver_iterate  enqueues `iterations` back-and-forth iterations on
+ *                       `stream` without synchronising; once the device has
+ *                       converged (or reached max_iter) further iterations do
+ *                       no work.
+ *   bfm_solver_finish   measures the current phi_n if the loop has not
+ *                       stopped, then fills `out` exactly as bfm_solve does
+ *                       (out->phi and out->psi must be the `phi`, `psi` of the
+ *                       earlier calls).  Synchronises the stream.
+ */
+bfm_status bfm_solver_init(const void *mu, const void *nu, const bfm_grid *grid, bfm_cost cost,
+                           bfm_precision prec, double tol, int max_iter, const bfm_options *opt,
+                           void *workspace, size_t workspace_bytes, void *stream,
+                           void *phi, void *psi);
+bfm_status bfm_solver_iterate(const bfm_grid *grid, bfm_precision prec, int max_iter,
+                              int iterations, void *workspace, size_t workspace_bytes,
+                              void *stream, void *phi, void *psi);
+bfm_status bfm_solver_finish(const bfm_grid *grid, bfm_precision prec, int max_iter,
+                             void *workspace, size_t workspace_bytes, void *stream,
+                             bfm_result *out);
+
+/*
+ * Per-launch timing of the library's kernels with CUDA events (this host
+ * thread only; the paper has no counterpart, it is measurement support).
+ * bfm_profile_begin(k) creates 2k events and starts recording one event pair
+ * around every kernel group the solver enqueues; bfm_profile_end waits for
+ * the recorded events and fills, for each kind 0..nkinds-1 (names from
+ * bfm_profile_kind_name), the summed milliseconds and the number of kernel
+ * launches; *dropped counts groups beyond k that were not recorded.
+ */
+int bfm_profile_kinds(void);
+const char *bfm_profile_kind_name(int kind);
+bfm_status bfm_profile_begin(int max_records);
+bfm_status bfm_profile_end(double *ms_by_kind, int *launches_by_kind, int nkinds, int *dropped);
+
 /* Workspace bytes for bfm_solve_host: bfm_workspace_bytes plus device room
  * for mu, nu, phi, psi and the map. */
 size_t bfm_workspace_bytes_host(const bfm_grid *grid, bfm_precision prec, int max_iter);

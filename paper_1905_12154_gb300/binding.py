@@ -83,6 +83,19 @@ _SIGS = {
     "bfm_map": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, _P]),
     "bfm_pushforward": (ctypes.c_int, [_P, _P, _P, _GP, ctypes.c_int, _P]),
     "bfm_interpolate": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _GP, ctypes.c_int, _P]),
+    "bfm_solver_init": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_int, ctypes.POINTER(bfm_options), _P,
+                                       ctypes.c_size_t, _P, _P, _P]),
+    "bfm_solver_iterate": (ctypes.c_int, [_GP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                          ctypes.c_size_t, _P, _P, _P]),
+    "bfm_solver_finish": (ctypes.c_int, [_GP, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t,
+                                         _P, ctypes.POINTER(bfm_result)]),
+    "bfm_profile_kinds": (ctypes.c_int, []),
+    "bfm_profile_kind_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "bfm_profile_begin": (ctypes.c_int, [ctypes.c_int]),
+    "bfm_profile_end": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
 }
 
 
@@ -332,3 +345,72 @@ def bfm_solve_host(mu: np.ndarray, nu: np.ndarray, tol: float = 1e-6, max_iter: 
     return dict(phi=phi, psi=psi, map=tmap, w2sq=res.w2sq, iters=it, converged=bool(res.converged),
                 status=s, dual=dual[:it + 1].copy(), resid=resid[:it + 1].copy(),
                 sigma=sig[:it + 1].copy(), max_mu=res.max_mu, max_nu=res.max_nu)
+
+
+class BfmSolver:
+    """Step-wise solve (bfm_solver_init / bfm_solver_iterate / bfm_solver_finish):
+    the caller decides when to iterate and when to read results.  phi and psi
+    are the device iterates; `workspace` holds all solver state."""
+
+    def __init__(self, mu, nu, tol: float = 0.0, max_iter: int = 1000, phi_init=None, **opts):
+        import torch
+        _dev(mu, "mu"); _dev(nu, "nu")
+        self.grid = grid_of(mu.shape)
+        self.prec = _prec(mu)
+        self.max_iter = int(max_iter)
+        self.shape = tuple(mu.shape)
+        self.phi = torch.empty_like(mu)
+        self.psi = torch.empty_like(mu)
+        if phi_init is not None:
+            self.phi.copy_(phi_init)
+            opts["warm_start"] = 1
+        self.nbytes = lib().bfm_workspace_bytes(ctypes.byref(self.grid), self.prec, self.max_iter)
+        self._ws_keep, self._ws = _workspace(self.nbytes, mu.device)
+        o = _options(**opts)
+        _check(lib().bfm_solver_init(mu.data_ptr(), nu.data_ptr(), ctypes.byref(self.grid),
+                                     BFM_COST_QUADRATIC, self.prec, float(tol), self.max_iter,
+                                     ctypes.byref(o), self._ws, self.nbytes, _stream(),
+                                     self.phi.data_ptr(), self.psi.data_ptr()),
+               "bfm_solver_init")
+
+    def iterate(self, k: int = 1):
+        _check(lib().bfm_solver_iterate(ctypes.byref(self.grid), self.prec, self.max_iter, int(k),
+                                        self._ws, self.nbytes, _stream(), self.phi.data_ptr(),
+                                        self.psi.data_ptr()), "bfm_solver_iterate")
+
+    def finish(self, with_map: bool = True) -> dict:
+        import torch
+        nd = len(self.shape)
+        tmap = torch.empty((nd,) + self.shape, dtype=self.phi.dtype, device=self.phi.device) if with_map else None
+        L = self.max_iter + 1
+        dual = np.zeros(L); resid = np.zeros(L); sig = np.zeros(L)
+        res = bfm_result()
+        res.phi = self.phi.data_ptr(); res.psi = self.psi.data_ptr()
+        res.map = tmap.data_ptr() if with_map else None
+        res.dual = dual.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        res.resid = resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        res.sigma = sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        s = lib().bfm_solver_finish(ctypes.byref(self.grid), self.prec, self.max_iter, self._ws,
+                                    self.nbytes, _stream(), ctypes.byref(res))
+        _check(s, "bfm_solver_finish", ok=(BFM_OK, BFM_NOT_CONVERGED))
+        it = res.iters
+        return dict(phi=self.phi, psi=self.psi, map=tmap, w2sq=res.w2sq, iters=it,
+                    converged=bool(res.converged), status=s, dual=dual[:it + 1].copy(),
+                    resid=resid[:it + 1].copy(), sigma=sig[:it + 1].copy(),
+                    max_mu=res.max_mu, max_nu=res.max_nu)
+
+
+def bfm_profile_begin(max_records: int = 4096):
+    _check(lib().bfm_profile_begin(int(max_records)), "bfm_profile_begin")
+
+
+def bfm_profile_end() -> dict:
+    """{kind name: (milliseconds, kernel launches)} since bfm_profile_begin."""
+    k = lib().bfm_profile_kinds()
+    ms = (ctypes.c_double * k)()
+    cnt = (ctypes.c_int * k)()
+    dropped = ctypes.c_int(0)
+    _check(lib().bfm_profile_end(ms, cnt, k, ctypes.byref(dropped)), "bfm_profile_end")
+    out = {lib().bfm_profile_kind_name(i).decode(): (ms[i], cnt[i]) for i in range(k)}
+    out["_dropped"] = (0.0, dropped.value)
+    return out

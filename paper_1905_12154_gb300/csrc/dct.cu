@@ -336,21 +336,28 @@ size_t axis_table_bytes(int n, int elem_bytes)
     return up((size_t)n * 2 * elem_bytes) * 2 + up((size_t)n * 2) + up((size_t)n * 8);
 }
 
-template <typename T>
-bfm_status fill_axis_tables(int n, AxisTables* t, unsigned char* ws, cudaStream_t st)
+bool layout_axis_tables(int n, int elem_bytes, unsigned char* ws, AxisTables* t)
 {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     FftRadices rs;
-    if (!fft_radices(n, &rs)) return BFM_ERR_UNSUPPORTED;
+    if (!fft_radices(n, &rs)) return false;
+    const size_t cb = up((size_t)n * 2 * elem_bytes);
     t->n = n;
     t->rs = rs;
     t->tw = ws;
-    t->dtw = ws + up((size_t)n * 2 * sizeof(T));
-    t->drev = reinterpret_cast<unsigned short*>(ws + 2 * up((size_t)n * 2 * sizeof(T)));
-    t->lam = reinterpret_cast<double*>(ws + 2 * up((size_t)n * 2 * sizeof(T)) + up((size_t)n * 2));
+    t->dtw = ws + cb;
+    t->drev = reinterpret_cast<unsigned short*>(ws + 2 * cb);
+    t->lam = reinterpret_cast<double*>(ws + 2 * cb + up((size_t)n * 2));
+    return true;
+}
+
+template <typename T>
+bfm_status fill_axis_tables(int n, AxisTables* t, unsigned char* ws, cudaStream_t st)
+{
+    if (!layout_axis_tables(n, (int)sizeof(T), ws, t)) return BFM_ERR_UNSUPPORTED;
     fill_tables_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(
         n, reinterpret_cast<cx_t<T>*>(t->tw), reinterpret_cast<cx_t<T>*>(t->dtw), t->drev, t->lam,
-        rs.nst, rs);
+        t->rs.nst, t->rs);
     BFM_LAUNCH_CHECK("fill_tables_kernel");
     return BFM_OK;
 }
@@ -402,6 +409,12 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
 {
     DctPlan p = plan_dct_pass(g, axis, (int)sizeof(T));
     const AxisTables& tb = tabs[axis];
+    // host-side guard: never launch with tables that do not describe this axis
+    if (tb.n != g.n[axis] || !tb.tw || !tb.dtw || !tb.drev || !tb.lam || tb.rs.nst < 1 ||
+        !tabs[0].lam || (g.ndim == 3 && !tabs[1].lam)) {
+        set_last_error("internal: DCT tables do not match the grid");
+        return BFM_ERR_INVALID_ARG;
+    }
     DctArgs<T> a;
     a.in = in; a.base = base; a.out = out; a.upd = upd; a.sigma = sigma; a.part = part;
     a.done = done;

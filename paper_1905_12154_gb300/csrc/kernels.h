@@ -41,6 +41,9 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
 
 bool fft_radices(int n, FftRadices* rs);
 size_t axis_table_bytes(int n, int elem_bytes);
+// Pointers and radices of one axis's tables inside `ws` (deterministic, so any
+// view of a workspace can rebuild them without touching the device).
+bool layout_axis_tables(int n, int elem_bytes, unsigned char* ws, AxisTables* t);
 
 template <typename T>
 bfm_status fill_axis_tables(int n, AxisTables* t, unsigned char* ws, cudaStream_t st);

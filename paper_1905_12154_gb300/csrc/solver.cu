@@ -227,7 +227,9 @@ static void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Work
     w->parts = reinterpret_cast<double*>(p); p += up256(sizeof(double) * kPartialSlots * kMaxPartials);
     w->tables = p;
     for (int a = 0; a < g.ndim; ++a) {
-        w->tabs[a].tw = p;   // filled by fill_axis_tables
+        // every view of the workspace rebuilds the same table pointers; sizes
+        // were validated (2^p 3^q) before any workspace is carved
+        if (!layout_axis_tables(g.n[a], eb, p, &w->tabs[a])) memset(&w->tabs[a], 0, sizeof(AxisTables));
         p += axis_table_bytes(g.n[a], eb);
     }
     if (fields) {
@@ -265,6 +267,39 @@ static bool fft_sizes_ok(const Grid& g)
 static double* slot(Workspace* w, int s) { return w->parts + (size_t)s * kMaxPartials; }
 
 // ---------------------------------------------------------------------------
+// optional per-launch timing (bfm_profile_begin / bfm_profile_end)
+// ---------------------------------------------------------------------------
+enum {
+    PK_CT0 = 0, PK_CT1, PK_CT2, PK_DCT_FWD, PK_DCT_MID, PK_DCT_INV, PK_PUSH, PK_SMALL, PK_COUNT
+};
+static const char* kProfNames[PK_COUNT] = {
+    "ct_pass_axis0", "ct_pass_axis1", "ct_pass_axis2", "dct_fwd", "dct_mid", "dct_inv",
+    "pushforward", "reduce_step"};
+
+struct ProfRec { int kind; int launches; cudaEvent_t a, b; };
+struct Profiler {
+    bool on = false;
+    int cap = 0, used = 0, dropped = 0;
+    ProfRec* rec = nullptr;
+};
+static thread_local Profiler g_prof;
+
+struct ProfScope {
+    ProfRec* r = nullptr;
+    cudaStream_t st;
+    ProfScope(int kind, int launches, cudaStream_t s) : st(s)
+    {
+        if (!g_prof.on) return;
+        if (g_prof.used >= g_prof.cap) { g_prof.dropped++; return; }
+        r = &g_prof.rec[g_prof.used++];
+        r->kind = kind;
+        r->launches = launches;
+        cudaEventRecord(r->a, st);
+    }
+    ~ProfScope() { if (r) cudaEventRecord(r->b, st); }
+};
+
+// ---------------------------------------------------------------------------
 // the pieces of one half step
 // ---------------------------------------------------------------------------
 // c-transform out = src^c with the two dot products of the dual value.
@@ -276,6 +311,7 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
     for (int a = 0; a < g.ndim; ++a) {
         const bool first = (a == 0), last = (a == g.ndim - 1);
         int used = 0;
+        ProfScope ps(PK_CT0 + a, 1, st);
         bfm_status s = launch_ct_pass<T>(g, a, first ? src : out, out, first,
                                          first ? w_src : nullptr, first ? p_in : nullptr,
                                          last ? w_out : nullptr, last ? p_out : nullptr, done,
@@ -296,11 +332,13 @@ static bfm_status poisson_forward(const Grid& g, const AxisTables* tabs, const T
 {
     const int last = g.ndim - 1;
     for (int a = 0; a < last; ++a) {
+        ProfScope ps(PK_DCT_FWD, 1, st);
         bfm_status s = launch_dct_pass<T>(g, a, PASS_FWD, tabs, a == 0 ? in : buf,
                                           a == 0 ? base : nullptr, buf, nullptr, nullptr, nullptr,
                                           done, st, nullptr);
         if (s != BFM_OK) return s;
     }
+    ProfScope ps(PK_DCT_MID, 1, st);
     return launch_dct_pass<T>(g, last, PASS_MID, tabs, buf, nullptr, buf, nullptr, nullptr, p_g,
                               done, st, n_g);
 }
@@ -314,6 +352,7 @@ static bfm_status poisson_inverse(const Grid& g, const AxisTables* tabs, T* buf,
 {
     for (int a = g.ndim - 2; a >= 0; --a) {
         const bool final_ = (a == 0);
+        ProfScope ps(PK_DCT_INV, 1, st);
         bfm_status s = launch_dct_pass<T>(g, a, PASS_INV, tabs, buf, nullptr, final_ ? out : buf,
                                           final_ ? upd : nullptr, sigma, nullptr, done, st, nullptr);
         if (s != BFM_OK) return s;
@@ -342,22 +381,34 @@ static bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, 
     bfm_status s;
     s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st);
     if (s != BFM_OK) return s;
-    finalize_dual_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
-                                            phi_half ? 0 : 2, logs);
-    BFM_LAUNCH_CHECK("finalize_dual_kernel");
-    s = launch_pushforward<T>(g, tmp, source, rho, done, st);
-    if (s != BFM_OK) return s;
+    {
+        ProfScope ps(PK_SMALL, 1, st);
+        finalize_dual_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+                                                phi_half ? 0 : 2, logs);
+        BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    }
+    {
+        ProfScope ps(PK_PUSH, 1, st);
+        s = launch_pushforward<T>(g, tmp, source, rho, done, st);
+        if (s != BFM_OK) return s;
+    }
     s = poisson_forward<T>(g, w->tabs, rho, target, rho, slot(w, 2), &ng, done, st);
     if (s != BFM_OK) return s;
-    finalize_G_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 2), ng, phi_half ? 0 : 1, logs);
-    BFM_LAUNCH_CHECK("finalize_G_kernel");
+    {
+        ProfScope ps(PK_SMALL, 1, st);
+        finalize_G_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 2), ng, phi_half ? 0 : 1, logs);
+        BFM_LAUNCH_CHECK("finalize_G_kernel");
+    }
     s = poisson_inverse<T>(g, w->tabs, rho, src, src, &w->state->sigma, done, st);
     if (s != BFM_OK) return s;
     s = ct_with_dots<T>(g, src, dst, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st);
     if (s != BFM_OK) return s;
-    finalize_dual_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
-                                            phi_half ? 1 : 3, logs);
-    BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    {
+        ProfScope ps(PK_SMALL, 1, st);
+        finalize_dual_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+                                                phi_half ? 1 : 3, logs);
+        BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    }
     return BFM_OK;
 }
 
@@ -377,15 +428,31 @@ static bfm_status measure_density(const Grid& g, const T* x, Workspace* w, int w
 
 static int elem_bytes(bfm_precision p) { return p == BFM_FP64 ? 8 : 4; }
 
+static Logs logs_of(Workspace* w, int max_iter)
+{
+    Logs logs;
+    const int L = max_iter + 1;
+    logs.dual = w->logs;
+    logs.resid = w->logs + L;
+    logs.sigma = w->logs + 2 * L;
+    return logs;
+}
+
+__global__ void stop_now_kernel(SolverState* st)
+{
+    if (threadIdx.x == 0 && !st->done) st->max_iter = st->iter;
+}
+
+// Setup: validate and normalise the densities, fill the tables, measure
+// ||nu - 1||^2_{H^-1}, set phi_0 (= 0 unless warm-started) and the state.
 template <typename T>
-static bfm_status solve_impl(const T* mu, const T* nu, const Grid& g, double tol, int max_iter,
-                             const bfm_options& o, unsigned char* wsp, cudaStream_t st,
-                             bfm_result* out)
+static bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int max_iter,
+                            const bfm_options& o, unsigned char* wsp, cudaStream_t st, T* phi,
+                            T* psi)
 {
     Workspace w;
     carve(g, sizeof(T), max_iter, wsp, &w, true);
     bfm_status s;
-    // -- input checks and normalisation -----------------------------------------
     s = measure_density<T>(g, mu, &w, 0, st); if (s != BFM_OK) return s;
     s = measure_density<T>(g, nu, &w, 1, st); if (s != BFM_OK) return s;
     SolverState hs;
@@ -406,45 +473,68 @@ static bfm_status solve_impl(const T* mu, const T* nu, const Grid& g, double tol
                                        o.alpha1, o.alpha2, o.sigma_min);
     BFM_LAUNCH_CHECK("init_state_kernel");
     s = fill_tables<T>(g, &w, st); if (s != BFM_OK) return s;
-    // -- ||nu - 1||^2_{H^-1}: the mean of nu/mass is 1 and the zero mode is dropped
+    // ||nu - 1||^2_{H^-1}: the mean of nu/mass is 1 and the zero mode is dropped
     int ng = 0;
     s = poisson_forward<T>(g, w.tabs, (const T*)w.nu_n, nullptr, (T*)w.rho, slot(&w, 2), &ng,
                            nullptr, st);
     if (s != BFM_OK) return s;
-    Logs logs;
-    const int L = max_iter + 1;
-    logs.dual = w.logs;
-    logs.resid = w.logs + L;
-    logs.sigma = w.logs + 2 * L;
+    Logs logs = logs_of(&w, max_iter);
     finalize_G_kernel<<<1, 256, 0, st>>>(w.state, slot(&w, 2), ng, 2, logs);
     BFM_LAUNCH_CHECK("finalize_G_kernel");
-    T* phi = (T*)out->phi;
-    T* psi = (T*)out->psi;
     if (!o.warm_start) BFM_CUDA(cudaMemsetAsync(phi, 0, sizeof(T) * g.N, st));
     BFM_CUDA(cudaMemsetAsync(psi, 0, sizeof(T) * g.N, st));
-    BFM_CUDA(cudaMemsetAsync(w.logs, 0, sizeof(double) * 3 * L, st));
-    // -- iterations --------------------------------------------------------------------
-    const int poll = o.poll_every > 0 ? o.poll_every : 4;
-    int enq = 0;
-    while (enq <= max_iter) {
-        const int chunk = (max_iter + 1 - enq) < poll ? (max_iter + 1 - enq) : poll;
-        for (int c = 0; c < chunk; ++c) {
-            s = half_step<T>(g, &w, true, phi, psi, logs, st); if (s != BFM_OK) return s;
-            s = half_step<T>(g, &w, false, phi, psi, logs, st); if (s != BFM_OK) return s;
-        }
-        enq += chunk;
-        int done = 0;
-        BFM_CUDA(cudaMemcpyAsync(&done, &w.state->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-        BFM_CUDA(cudaStreamSynchronize(st));
-        if (done) break;
+    BFM_CUDA(cudaMemsetAsync(w.logs, 0, sizeof(double) * 3 * (max_iter + 1), st));
+    return BFM_OK;
+}
+
+// Enqueue `iters` back-and-forth iterations; no host synchronisation.
+template <typename T>
+static bfm_status iterate_impl(const Grid& g, int max_iter, int iters, unsigned char* wsp,
+                               cudaStream_t st, T* phi, T* psi)
+{
+    Workspace w;
+    carve(g, sizeof(T), max_iter, wsp, &w, true);
+    Logs logs = logs_of(&w, max_iter);
+    for (int c = 0; c < iters; ++c) {
+        bfm_status s = half_step<T>(g, &w, true, phi, psi, logs, st); if (s != BFM_OK) return s;
+        s = half_step<T>(g, &w, false, phi, psi, logs, st); if (s != BFM_OK) return s;
     }
+    return BFM_OK;
+}
+
+static bfm_status read_done(const Grid& g, int eb, int max_iter, unsigned char* wsp,
+                            cudaStream_t st, int* done)
+{
+    Workspace w;
+    carve(g, eb, max_iter, wsp, &w, true);
+    BFM_CUDA(cudaMemcpyAsync(done, &w.state->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BFM_CUDA(cudaStreamSynchronize(st));
+    return BFM_OK;
+}
+
+// Outputs: if the loop has not stopped, one more measurement (the first part
+// of a phi-half step) gives phi_n^c and J(phi_n); then psi = phi_n^c, the map
+// T = x - grad psi, W2^2 = 2 J(phi_n) and the logs.
+template <typename T>
+static bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, cudaStream_t st,
+                              bfm_result* out)
+{
+    Workspace w;
+    carve(g, sizeof(T), max_iter, wsp, &w, true);
+    Logs logs = logs_of(&w, max_iter);
+    T* phi = (T*)out->phi;
+    T* psi = (T*)out->psi;
+    stop_now_kernel<<<1, 32, 0, st>>>(w.state);
+    BFM_LAUNCH_CHECK("stop_now_kernel");
+    bfm_status s = half_step<T>(g, &w, true, phi, psi, logs, st);
+    if (s != BFM_OK) return s;
+    SolverState hs;
     BFM_CUDA(cudaMemcpyAsync(&hs, w.state, sizeof(hs), cudaMemcpyDeviceToHost, st));
     BFM_CUDA(cudaStreamSynchronize(st));
     if (hs.nonfinite) {
         set_last_error("a reduction produced a non-finite value");
         return BFM_ERR_NONFINITE;
     }
-    // -- outputs: phi_n, psi = phi_n^c (left in tmp by the last phi-half), the map
     BFM_CUDA(cudaMemcpyAsync(psi, w.tmp, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, st));
     if (out->map) { s = launch_map<T>(g, psi, (T*)out->map, st); if (s != BFM_OK) return s; }
     const int nlog = hs.iter + 1;
@@ -504,25 +594,33 @@ static bfm_status check_common(const bfm_grid* grid, bfm_precision prec, Grid* g
     return BFM_OK;
 }
 
-extern "C" bfm_status bfm_solve(const void* mu, const void* nu, const bfm_grid* grid, bfm_cost cost,
-                                bfm_precision prec, double tol, int max_iter, const bfm_options* opt,
-                                void* workspace, size_t workspace_bytes, void* stream,
-                                bfm_result* out)
+static bfm_status check_solver_args(const bfm_grid* grid, bfm_precision prec, int max_iter,
+                                    void* workspace, size_t workspace_bytes, Grid* g)
 {
-    Grid g;
-    bfm_status s = check_common(grid, prec, &g);
+    bfm_status s = check_common(grid, prec, g);
     if (s != BFM_OK) return s;
-    if (cost != BFM_COST_QUADRATIC) { set_last_error("only the quadratic cost is implemented"); return BFM_ERR_UNSUPPORTED; }
-    if (!fft_sizes_ok(g)) { set_last_error("every n[a] must be 2^p 3^q"); return BFM_ERR_UNSUPPORTED; }
-    if (!mu || !nu || !out || !out->phi || !out->psi || !(tol >= 0.0) || max_iter < 0 ||
-        max_iter > 10000000) {
-        set_last_error("null pointer, negative tolerance or bad max_iter");
-        return BFM_ERR_INVALID_ARG;
-    }
+    if (!fft_sizes_ok(*g)) { set_last_error("every n[a] must be 2^p 3^q"); return BFM_ERR_UNSUPPORTED; }
+    if (max_iter < 0 || max_iter > 10000000) { set_last_error("bad max_iter"); return BFM_ERR_INVALID_ARG; }
     if (!workspace || !aligned256(workspace) ||
-        workspace_bytes < solve_bytes(g, elem_bytes(prec), max_iter)) {
+        workspace_bytes < solve_bytes(*g, elem_bytes(prec), max_iter)) {
         set_last_error("workspace NULL, not 256-byte aligned or smaller than bfm_workspace_bytes()");
         return BFM_ERR_WORKSPACE;
+    }
+    return BFM_OK;
+}
+
+extern "C" bfm_status bfm_solver_init(const void* mu, const void* nu, const bfm_grid* grid,
+                                      bfm_cost cost, bfm_precision prec, double tol, int max_iter,
+                                      const bfm_options* opt, void* workspace,
+                                      size_t workspace_bytes, void* stream, void* phi, void* psi)
+{
+    Grid g;
+    bfm_status s = check_solver_args(grid, prec, max_iter, workspace, workspace_bytes, &g);
+    if (s != BFM_OK) return s;
+    if (cost != BFM_COST_QUADRATIC) { set_last_error("only the quadratic cost is implemented"); return BFM_ERR_UNSUPPORTED; }
+    if (!mu || !nu || !phi || !psi || !(tol >= 0.0)) {
+        set_last_error("null pointer or negative tolerance");
+        return BFM_ERR_INVALID_ARG;
     }
     bfm_options o;
     bfm_default_options(&o);
@@ -535,8 +633,122 @@ extern "C" bfm_status bfm_solve(const void* mu, const void* nu, const bfm_grid* 
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* wsp = (unsigned char*)workspace;
     if (prec == BFM_FP32)
-        return solve_impl<float>((const float*)mu, (const float*)nu, g, tol, max_iter, o, wsp, st, out);
-    return solve_impl<double>((const double*)mu, (const double*)nu, g, tol, max_iter, o, wsp, st, out);
+        return init_impl<float>((const float*)mu, (const float*)nu, g, tol, max_iter, o, wsp, st,
+                                (float*)phi, (float*)psi);
+    return init_impl<double>((const double*)mu, (const double*)nu, g, tol, max_iter, o, wsp, st,
+                             (double*)phi, (double*)psi);
+}
+
+extern "C" bfm_status bfm_solver_iterate(const bfm_grid* grid, bfm_precision prec, int max_iter,
+                                         int iterations, void* workspace, size_t workspace_bytes,
+                                         void* stream, void* phi, void* psi)
+{
+    Grid g;
+    bfm_status s = check_solver_args(grid, prec, max_iter, workspace, workspace_bytes, &g);
+    if (s != BFM_OK) return s;
+    if (!phi || !psi || iterations < 0) return BFM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* wsp = (unsigned char*)workspace;
+    if (prec == BFM_FP32)
+        return iterate_impl<float>(g, max_iter, iterations, wsp, st, (float*)phi, (float*)psi);
+    return iterate_impl<double>(g, max_iter, iterations, wsp, st, (double*)phi, (double*)psi);
+}
+
+extern "C" bfm_status bfm_solver_finish(const bfm_grid* grid, bfm_precision prec, int max_iter,
+                                        void* workspace, size_t workspace_bytes, void* stream,
+                                        bfm_result* out)
+{
+    Grid g;
+    bfm_status s = check_solver_args(grid, prec, max_iter, workspace, workspace_bytes, &g);
+    if (s != BFM_OK) return s;
+    if (!out || !out->phi || !out->psi) return BFM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* wsp = (unsigned char*)workspace;
+    if (prec == BFM_FP32) return finish_impl<float>(g, max_iter, wsp, st, out);
+    return finish_impl<double>(g, max_iter, wsp, st, out);
+}
+
+extern "C" bfm_status bfm_solve(const void* mu, const void* nu, const bfm_grid* grid, bfm_cost cost,
+                                bfm_precision prec, double tol, int max_iter, const bfm_options* opt,
+                                void* workspace, size_t workspace_bytes, void* stream,
+                                bfm_result* out)
+{
+    if (!out) return BFM_ERR_INVALID_ARG;
+    bfm_status s = bfm_solver_init(mu, nu, grid, cost, prec, tol, max_iter, opt, workspace,
+                                   workspace_bytes, stream, out->phi, out->psi);
+    if (s != BFM_OK) return s;
+    Grid g;
+    make_grid(grid, &g);
+    const int poll = (opt && opt->poll_every > 0) ? opt->poll_every : 4;
+    int enq = 0;
+    while (enq <= max_iter) {
+        const int chunk = (max_iter + 1 - enq) < poll ? (max_iter + 1 - enq) : poll;
+        s = bfm_solver_iterate(grid, prec, max_iter, chunk, workspace, workspace_bytes, stream,
+                               out->phi, out->psi);
+        if (s != BFM_OK) return s;
+        enq += chunk;
+        int done = 0;
+        s = read_done(g, elem_bytes(prec), max_iter, (unsigned char*)workspace,
+                      (cudaStream_t)stream, &done);
+        if (s != BFM_OK) return s;
+        if (done) break;
+    }
+    return bfm_solver_finish(grid, prec, max_iter, workspace, workspace_bytes, stream, out);
+}
+
+extern "C" int bfm_profile_kinds(void) { return PK_COUNT; }
+
+extern "C" const char* bfm_profile_kind_name(int kind)
+{
+    return (kind >= 0 && kind < PK_COUNT) ? kProfNames[kind] : "";
+}
+
+extern "C" bfm_status bfm_profile_begin(int max_records)
+{
+    if (max_records <= 0) return BFM_ERR_INVALID_ARG;
+    if (g_prof.on) return BFM_ERR_INVALID_ARG;
+    g_prof.rec = new ProfRec[max_records];
+    for (int i = 0; i < max_records; ++i) {
+        BFM_CUDA(cudaEventCreate(&g_prof.rec[i].a));
+        BFM_CUDA(cudaEventCreate(&g_prof.rec[i].b));
+    }
+    g_prof.cap = max_records;
+    g_prof.used = 0;
+    g_prof.dropped = 0;
+    g_prof.on = true;
+    return BFM_OK;
+}
+
+extern "C" bfm_status bfm_profile_end(double* ms_by_kind, int* launches_by_kind, int nkinds,
+                                      int* dropped)
+{
+    if (!g_prof.on) return BFM_ERR_INVALID_ARG;
+    g_prof.on = false;
+    bfm_status s = BFM_OK;
+    for (int k = 0; k < nkinds; ++k) {
+        if (ms_by_kind) ms_by_kind[k] = 0.0;
+        if (launches_by_kind) launches_by_kind[k] = 0;
+    }
+    for (int i = 0; i < g_prof.used; ++i) {
+        ProfRec& r = g_prof.rec[i];
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) { s = cuda_status(e, "bfm_profile_end"); continue; }
+        if (r.kind < nkinds) {
+            if (ms_by_kind) ms_by_kind[r.kind] += ms;
+            if (launches_by_kind) launches_by_kind[r.kind] += r.launches;
+        }
+    }
+    for (int i = 0; i < g_prof.cap; ++i) {
+        cudaEventDestroy(g_prof.rec[i].a);
+        cudaEventDestroy(g_prof.rec[i].b);
+    }
+    delete[] g_prof.rec;
+    g_prof.rec = nullptr;
+    if (dropped) *dropped = g_prof.dropped;
+    g_prof.cap = g_prof.used = 0;
+    return s;
 }
 
 extern "C" bfm_status bfm_solve_host(const void* mu, const void* nu, const bfm_grid* grid,

@@ -225,3 +225,50 @@ def test_solve_max_iter_zero(B):
     ref = oracle.solve(mu, nu, tol=0.0, max_iter=0)
     assert r["iters"] == 0 and r["status"] == B.BFM_NOT_CONVERGED
     assert abs(r["resid"][0] - ref["resid"][0]) < 1e-12
+
+
+def test_stepwise_solver_matches_solve(B):
+    """bfm_solver_init / iterate / finish give exactly what bfm_solve gives."""
+    mu, nu = si.workload_gauss_disc_64(32)
+    r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=7)
+    s = B.BfmSolver(dev(mu), dev(nu), tol=0.0, max_iter=7)
+    s.iterate(3)
+    s.iterate(2)
+    q = s.finish()                 # stops at iteration 5 and measures phi_5
+    ref5 = oracle.solve(mu, nu, tol=0.0, max_iter=5)
+    assert q["iters"] == 5
+    assert abs(q["w2sq"] - ref5["w2sq"]) < 1e-12
+    assert np.max(np.abs(q["resid"] - ref5["resid"])) < 1e-9
+    s2 = B.BfmSolver(dev(mu), dev(nu), tol=0.0, max_iter=7)
+    s2.iterate(20)                 # iterations past max_iter do no work
+    q2 = s2.finish()
+    assert q2["iters"] == r["iters"] == 7
+    # the pushforward's atomic adds land in any order, so equal up to rounding
+    assert abs(q2["w2sq"] - r["w2sq"]) < 1e-14
+    assert torch.max(torch.abs(q2["phi"] - r["phi"])).item() < 1e-12
+    assert torch.max(torch.abs(q2["psi"] - r["psi"])).item() < 1e-12
+
+
+def test_warm_start(B):
+    """Resuming from phi_n (checkpoint/resume) continues the iteration."""
+    mu, nu = si.translated_discs(32)
+    r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=3)
+    r2 = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=3, phi_init=r["phi"])
+    assert r2["dual"][0] == pytest.approx(r["dual"][-1], abs=1e-14)
+    assert r2["w2sq"] >= r["w2sq"] - 1e-12
+
+
+def test_profiler_counts_launches(B):
+    mu, nu = si.translated_discs(32)
+    s = B.BfmSolver(dev(mu), dev(nu), tol=0.0, max_iter=10)
+    B.bfm_profile_begin(200)
+    s.iterate(2)
+    prof = B.bfm_profile_end()
+    # per iteration in 2D: 8 c-transform passes, 2 pushforwards, 2 x (fwd, mid, inv)
+    # DCT passes, 6 reduction/step kernels
+    assert prof["ct_pass_axis0"][1] == 8 and prof["ct_pass_axis1"][1] == 8
+    assert prof["pushforward"][1] == 4
+    assert prof["dct_fwd"][1] == prof["dct_mid"][1] == prof["dct_inv"][1] == 4
+    assert prof["reduce_step"][1] == 12
+    assert prof["_dropped"][1] == 0
+    assert all(v[0] > 0 for k, v in prof.items() if not k.startswith("_") and v[1])
