@@ -539,7 +539,8 @@ static double step_rule(double sigma, double gain, double G, const oracle_opts *
  *              I_new = I(psi); update sigma.
  * Reading: one shared sigma updated after every half step; the residual is
  * the H^-1 norm of nu - T#mu relative to that of nu - 1 (mu and nu have unit
- * mass so their mean is 1); it is measured at the start of each iteration.
+ * mass so their mean is 1); it is measured at the start of each iteration;
+ * when nu is uniform (||nu - 1|| = 0) the absolute residual sqrt(G) is used.
  * Logs (length max_iter+1, may be NULL): dual[n] = J(phi_n), resid[n] = r_n,
  * sig[n] = sigma at the start of iteration n; half (length 3*max_iter) holds
  * half[3n..3n+2] = (J(phi_{n+1/2}), I(psi_{n+1/2}), I(psi_{n+1})); J(phi_{n+1})
@@ -589,7 +590,7 @@ int bfm_oracle_solve(const double *mu_in, const double *nu_in, int ndim, const i
         for (long i = 0; i < N; i++) f[i] = nu[i] - rho[i];
         double G;
         bfm_oracle_poisson(f, gr, ndim, n, o.dct_mode, &G);
-        double r = (Gref > 0) ? sqrt(fmax(G, 0.0) / Gref) : 0.0;
+        double r = (Gref > 0) ? sqrt(fmax(G, 0.0) / Gref) : sqrt(fmax(G, 0.0));
         if (dual) dual[it] = Jold;
         if (resid) resid[it] = r;
         if (sig) sig[it] = sigma;
