@@ -35,8 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "BFM iterations/s (4096^2 FP32, FP64 reductions)"
 UNIT = "iter/s"
 
-# algorithmic bytes per grid cell of one launch, FP32 fields (each input read
-# and each output written once); see DESIGN.md "Algorithmic bytes"
+# algorithmic bytes per grid cell of one launch, FP32 fields: each input read
+# once and each output written once
 BYTES_PER_CELL_2D = {
     "ct_pass_axis0": 12,   # read phi, read weight (dual dot), write
     "ct_pass_axis1": 12,   # read, write, read weight (dual dot)
