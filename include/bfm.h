@@ -214,6 +214,25 @@ bfm_status bfm_poisson(const void *f, void *g, const bfm_grid *grid, bfm_precisi
                        double *G_out, void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * bfm_poisson without a workspace, for callers that cannot allocate device
+ * memory (their device memory is owned by another allocator, or allocating
+ * after start-up is forbidden because cudaMalloc/cudaFree synchronise the
+ * device).  The paper has no counterpart: it is a memory-management variant of
+ * bfm_poisson and computes the same g and G (same arguments, same meaning).
+ * Its scratch is a 1 MiB array built into the library (one per device, kept
+ * until the process exits), which holds every 2D or 3D grid with at most 4096
+ * cells per axis in either precision; a grid that needs more scratch returns
+ * BFM_ERR_UNSUPPORTED.  The call allocates no device memory.
+ * The first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture begins.
+ * Every call on a device uses the same array: calls whose GPU work overlaps
+ * (different streams or host threads) race and must be serialised by the
+ * caller.
+ */
+bfm_status bfm_poisson_noalloc(const void *f, void *g, const bfm_grid *grid, bfm_precision prec,
+                               double *G_out, void *stream);
+
+/*
  * The map of Lemma 2.2(ii) for the quadratic cost, T(x) = x - grad psi(x),
  * with grad psi by central differences (one-sided at the first and last cell
  * of each line) and T clamped to the box of cell centres.

@@ -80,6 +80,8 @@ _SIGS = {
     "bfm_ctransform": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, _P]),
     "bfm_poisson": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    _P, ctypes.c_size_t, _P]),
+    "bfm_poisson_noalloc": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double), _P]),
     "bfm_map": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, _P]),
     "bfm_pushforward": (ctypes.c_int, [_P, _P, _P, _GP, ctypes.c_int, _P]),
     "bfm_interpolate": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _GP, ctypes.c_int, _P]),
@@ -230,6 +232,18 @@ def bfm_poisson(f, out=None, want_G: bool = True):
            "bfm_poisson")
     del keep
     return out, (G.value if want_G else None)
+
+
+def bfm_poisson_noalloc(f, out=None):
+    """bfm_poisson without a workspace (the library's built-in scratch); returns (g, G)."""
+    import torch
+    _dev(f, "f")
+    out = torch.empty_like(f) if out is None else _dev(out, "out")
+    g = grid_of(f.shape)
+    G = ctypes.c_double(0.0)
+    _check(lib().bfm_poisson_noalloc(f.data_ptr(), out.data_ptr(), ctypes.byref(g), _prec(f),
+                                     ctypes.byref(G), _stream()), "bfm_poisson_noalloc")
+    return out, G.value
 
 
 def bfm_map(psi, out=None):

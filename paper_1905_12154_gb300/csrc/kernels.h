@@ -66,4 +66,9 @@ template <typename T>
 bfm_status launch_interpolate(const Grid& g, const T* map, const T* mu, double t, T* rho,
                               cudaStream_t st);
 
+// solver.cu: the Poisson solve on an explicit scratch block
+size_t poisson_scratch_bytes(const Grid& g, int eb);
+bfm_status poisson_on_scratch(const void* f, void* g_out, const Grid& g, bfm_precision prec,
+                              double* G_out, unsigned char* scratch, cudaStream_t st);
+
 }  // namespace bfm

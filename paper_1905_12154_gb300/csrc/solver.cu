@@ -832,6 +832,20 @@ static bfm_status poisson_impl(const T* f, T* gout, const Grid& g, double* G_out
     return BFM_OK;
 }
 
+namespace bfm {
+// The Poisson solve of bfm_poisson run on a caller-chosen scratch block (used
+// by the allocation-free entry point of noalloc.cu).
+size_t poisson_scratch_bytes(const Grid& g, int eb) { return poisson_bytes(g, eb); }
+
+bfm_status poisson_on_scratch(const void* f, void* g_out, const Grid& g, bfm_precision prec,
+                              double* G_out, unsigned char* scratch, cudaStream_t st)
+{
+    if (prec == BFM_FP32)
+        return poisson_impl<float>((const float*)f, (float*)g_out, g, G_out, scratch, st);
+    return poisson_impl<double>((const double*)f, (double*)g_out, g, G_out, scratch, st);
+}
+}  // namespace bfm
+
 extern "C" bfm_status bfm_poisson(const void* f, void* g_out, const bfm_grid* grid,
                                   bfm_precision prec, double* G_out, void* workspace,
                                   size_t workspace_bytes, void* stream)
