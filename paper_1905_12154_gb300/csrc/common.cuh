@@ -152,6 +152,51 @@ __device__ inline double block_max(double v, double* scratch32)
 }
 
 // ---------------------------------------------------------------------------
+// Per-thread dot-product / sum accumulator.  FP64 arithmetic runs at a small
+// fraction of the FP32 rate, so FP32 terms are accumulated in FP32 with
+// error-free transformations (the exact product a*b = p + e via one FMA, and a
+// compensated sum of the p's), which keeps about twice FP32 precision; the
+// partial is widened to FP64 once per tile and every reduction beyond the
+// thread is FP64.  FP64 terms are summed in FP64.
+// ---------------------------------------------------------------------------
+template <typename T> struct Acc;
+
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    // explicitly rounded operations: the compiler must not fuse or reorder them
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);                     // a*b - p exactly
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ void add(float a)
+    {
+        const float t = __fadd_rn(s, a);
+        const float z = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(a, z)));
+        s = t;
+    }
+    __device__ __forceinline__ double take()
+    {
+        const double v = (double)s + (double)c;
+        s = 0.f; c = 0.f;
+        return v;
+    }
+};
+
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ void add(double a) { s += a; }
+    __device__ __forceinline__ double take() { const double v = s; s = 0.0; return v; }
+};
+
+// ---------------------------------------------------------------------------
 // complex helpers
 // ---------------------------------------------------------------------------
 template <typename T> struct Cx;

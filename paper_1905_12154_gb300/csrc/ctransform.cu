@@ -42,12 +42,25 @@ struct CtArgs {
     int LDI;              // shared leading dimension of the index arrays
     T hh;                 // h^2 / 2 on this axis
     int negate;           // the pass reads -in
+    int vec4;             // rows may be moved as float4 (n % 4 == 0, 16-byte aligned)
+    int lw;               // log2(W); interleaved tiles have W a power of two
 };
 
-template <typename T>
+// Shared-memory layout of a line: thread t owns cells [tK, tK+K).  Stored
+// plainly, the threads of a warp would touch cells K apart, a K-way bank
+// conflict; one pad word per chunk for the values (two shorts for the index
+// stacks) makes the per-thread stride odd, so the threads of a warp hit
+// distinct banks.
+template <int K> struct Skew {
+    static constexpr int lg = (K >= 16) ? 4 : (K >= 8) ? 3 : (K >= 4) ? 2 : (K >= 2) ? 1 : 0;
+    __device__ __forceinline__ static int f(int p) { return p + (p >> lg); }
+    __device__ __forceinline__ static int s(int p) { return p + 2 * (p >> lg); }
+};
+
+template <int K, typename T>
 __device__ __forceinline__ bool hidden(const T* f, int a, int b, int c, T hh)
 {
-    const T fa = f[a], fb = f[b], fc = f[c];
+    const T fa = f[Skew<K>::f(a)], fb = f[Skew<K>::f(b)], fc = f[Skew<K>::f(c)];
     const T lhs = (fb - fa) * (T)(c - b) - (fc - fb) * (T)(b - a);
     const T rhs = hh * (T)(c - a) * (T)(b - a) * (T)(c - b);
     return lhs >= rhs;
@@ -60,57 +73,93 @@ __device__ __forceinline__ T parab(T hh, int x, int j, T fj)
     return fma(hh, (T)(d * d), fj);
 }
 
-// Phase B: merge the envelopes of thread groups [t, t+s) and [t+s, t+2s).
 template <typename T>
+__device__ __forceinline__ bool hidden_v(int a, T fa, int b, T fb, int c, T fc, T hh)
+{
+    const T lhs = (fb - fa) * (T)(c - b) - (fc - fb) * (T)(b - a);
+    const T rhs = hh * (T)(c - a) * (T)(b - a) * (T)(c - b);
+    return lhs >= rhs;
+}
+
+// Phase B: merge the envelopes of thread groups [t, t+s) and [t+s, t+2s).
+// beg/end hold chunk-space positions into the stack.  The left chain's last
+// two parabolas (a, b) and the right chain's first two (c, d) are kept in
+// registers with their stack positions, so each pop costs one stack read and
+// one value read; emptied segments are written back as they are passed.
+template <int K, typename T>
 __device__ void merge_pair(const T* f, const short* stk, short* beg, short* end,
                            int t, int s, int n, T hh)
 {
-    const int tl = t, tr = t + 2 * s;
-    int lt = t + s - 1;
+    using SK = Skew<K>;
+    const int tl = t, tm = t + s, tr = t + 2 * s;
+    int lt = tm - 1;
     while (lt >= tl && beg[lt] == end[lt]) --lt;
-    int rt = t + s;
+    int rt = tm;
     while (rt < tr && beg[rt] == end[rt]) ++rt;
     if (lt < tl || rt >= tr) return;
-    for (int guard = 0; guard <= n + 2; ++guard) {
-        const int b = stk[end[lt] - 1];
-        const int c = stk[beg[rt]];
-        int a = -1;
-        if (end[lt] - beg[lt] >= 2) {
-            a = stk[end[lt] - 2];
-        } else {
-            int la = lt - 1;
-            while (la >= tl && beg[la] == end[la]) --la;
-            if (la >= tl) a = stk[end[la] - 1];
-        }
-        if (a >= 0 && hidden(f, a, b, c, hh)) {
-            end[lt] = (short)(end[lt] - 1);
-            while (lt >= tl && beg[lt] == end[lt]) --lt;
-            if (lt < tl) return;
-            continue;
-        }
-        int d = -1;
-        if (end[rt] - beg[rt] >= 2) {
-            d = stk[beg[rt] + 1];
-        } else {
-            int ra = rt + 1;
-            while (ra < tr && beg[ra] == end[ra]) ++ra;
-            if (ra < tr) d = stk[beg[ra]];
-        }
-        if (d >= 0 && hidden(f, b, c, d, hh)) {
-            beg[rt] = (short)(beg[rt] + 1);
-            while (rt < tr && beg[rt] == end[rt]) ++rt;
-            if (rt >= tr) return;
-            continue;
-        }
-        return;
+    // left: b at (lt, pb), a at (la, pa)
+    int pb = end[lt] - 1;
+    int la = lt, pa = pb - 1, begla = beg[lt];
+    if (pa < begla) {
+        la = lt - 1;
+        while (la >= tl && beg[la] == end[la]) --la;
+        if (la >= tl) { pa = end[la] - 1; begla = beg[la]; } else pa = -1;
     }
+    // right: c at (rt, pc), d at (rd, pd)
+    int pc = beg[rt];
+    int rd = rt, pd = pc + 1, endrd = end[rt];
+    if (pd >= endrd) {
+        rd = rt + 1;
+        while (rd < tr && beg[rd] == end[rd]) ++rd;
+        if (rd < tr) { pd = beg[rd]; endrd = end[rd]; } else pd = -1;
+    }
+    int ib = stk[SK::s(pb)], ic = stk[SK::s(pc)];
+    int ia = pa >= 0 ? (int)stk[SK::s(pa)] : -1;
+    int id = pd >= 0 ? (int)stk[SK::s(pd)] : -1;
+    T fb = f[SK::f(ib)], fc = f[SK::f(ic)];
+    T fa = ia >= 0 ? f[SK::f(ia)] : (T)0;
+    T fd = id >= 0 ? f[SK::f(id)] : (T)0;
+    for (int guard = 0; guard <= n + 2; ++guard) {
+        if (ia >= 0 && hidden_v(ia, fa, ib, fb, ic, fc, hh)) {
+            // pop b; if it was the last parabola of thread lt, that segment empties
+            if (la != lt) { end[lt] = beg[lt]; lt = la; }
+            pb = pa; ib = ia; fb = fa;
+            pa = pa - 1;
+            if (pa < begla) {
+                la = la - 1;
+                while (la >= tl && beg[la] == end[la]) --la;
+                if (la >= tl) { pa = end[la] - 1; begla = beg[la]; } else pa = -1;
+            }
+            ia = pa >= 0 ? (int)stk[SK::s(pa)] : -1;
+            fa = ia >= 0 ? f[SK::f(ia)] : (T)0;
+            continue;
+        }
+        if (id >= 0 && hidden_v(ib, fb, ic, fc, id, fd, hh)) {
+            // pop c; if it was the last parabola of thread rt, that segment empties
+            if (rd != rt) { beg[rt] = end[rt]; rt = rd; }
+            pc = pd; ic = id; fc = fd;
+            pd = pd + 1;
+            if (pd >= endrd) {
+                rd = rd + 1;
+                while (rd < tr && beg[rd] == end[rd]) ++rd;
+                if (rd < tr) { pd = beg[rd]; endrd = end[rd]; } else pd = -1;
+            }
+            id = pd >= 0 ? (int)stk[SK::s(pd)] : -1;
+            fd = id >= 0 ? f[SK::f(id)] : (T)0;
+            continue;
+        }
+        break;
+    }
+    end[lt] = (short)(pb + 1);
+    beg[rt] = (short)pc;
 }
 
 template <typename T, int K, bool CONTIG>
-__global__ void __launch_bounds__(1024, 1) ct_pass_kernel(CtArgs<T> a)
+__global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a)
 {
     if (a.done && *a.done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    using SK = Skew<K>;
     const LineTiles& lt = a.lt;
     const int n = lt.n;
     const int G = a.G;
@@ -138,29 +187,68 @@ __global__ void __launch_bounds__(1024, 1) ct_pass_kernel(CtArgs<T> a)
     const int hi = min(lo + K, n);
 
     double acc_in = 0.0, acc_out = 0.0;
+    Acc<T> acc_t_in, acc_t_out;
 
     for (long long tile = blockIdx.x; tile < lt.ntiles; tile += gridDim.x) {
         const Tile tl = tile_at(lt, tile);
-        const int total = tl.wact * n;
         // ---- load ----------------------------------------------------------
-        for (int e = tid; e < total; e += blockDim.x) {
-            int ww, p;
-            if (CONTIG) { ww = e / n; p = e - ww * n; }
-            else        { p = e / tl.wact; ww = e - p * tl.wact; }
-            const long long ad = addr_of(lt, tl, ww, p);
-            const T v = a.in[ad];
-            fs[(size_t)ww * a.LD + p] = a.negate ? -v : v;
-            if (a.w_in) acc_in += (double)v * (double)a.w_in[ad];
+        if (CONTIG) {
+            for (int ww = 0; ww < tl.wact; ++ww) {
+                const long long rb = tl.base0 + (long long)ww * n;
+                T* frow = fs + (size_t)ww * a.LD;
+                if (sizeof(T) == 4 && a.vec4) {
+                    const float4* src = reinterpret_cast<const float4*>(a.in + rb);
+                    const float4* wsrc = reinterpret_cast<const float4*>(a.w_in + rb);
+                    for (int q = tid; q < (n >> 2); q += blockDim.x) {
+                        float4 v = src[q];
+                        if (a.w_in) {
+                            const float4 u = wsrc[q];
+                            acc_t_in.add_prod(v.x, u.x); acc_t_in.add_prod(v.y, u.y);
+                            acc_t_in.add_prod(v.z, u.z); acc_t_in.add_prod(v.w, u.w);
+                        }
+                        if (a.negate) { v.x = -v.x; v.y = -v.y; v.z = -v.z; v.w = -v.w; }
+                        frow[SK::f(4 * q)] = v.x;     frow[SK::f(4 * q + 1)] = v.y;
+                        frow[SK::f(4 * q + 2)] = v.z; frow[SK::f(4 * q + 3)] = v.w;
+                    }
+                } else {
+                    for (int p = tid; p < n; p += blockDim.x) {
+                        const T v = a.in[rb + p];
+                        if (a.w_in) acc_t_in.add_prod(v, a.w_in[rb + p]);
+                        frow[SK::f(p)] = a.negate ? -v : v;
+                    }
+                }
+            }
+        } else {
+            const int total = n << a.lw;
+            for (int e = tid; e < total; e += blockDim.x) {
+                const int p = e >> a.lw, ww = e & (W - 1);
+                if (ww < tl.wact) {
+                    const long long ad = tl.base0 + ww + (long long)p * lt.es;
+                    const T v = a.in[ad];
+                    if (a.w_in) acc_t_in.add_prod(v, a.w_in[ad]);
+                    fs[(size_t)ww * a.LD + SK::f(p)] = a.negate ? -v : v;
+                }
+            }
         }
         __syncthreads();
         const bool active = (w < tl.wact);
         // ---- A: envelope of this thread's chunk ------------------------------
         if (active) {
             if (lo < n) {
-                int top = lo - 1;
-                for (int q = lo; q < hi; ++q) {
-                    while (top >= lo + 1 && hidden(f, (int)stk[top - 1], (int)stk[top], q, hh)) --top;
-                    stk[++top] = (short)q;
+                // the top two stack entries live in registers
+                int top = lo;                          // chunk-space position of the top
+                int s1 = lo, s0 = -1;                  // top, second
+                stk[SK::s(lo)] = (short)lo;
+                for (int q = lo + 1; q < hi; ++q) {
+                    while (s0 >= 0 && hidden<K>(f, s0, s1, q, hh)) {
+                        --top;
+                        s1 = s0;
+                        s0 = (top > lo) ? (int)stk[SK::s(top - 1)] : -1;
+                    }
+                    ++top;
+                    stk[SK::s(top)] = (short)q;
+                    s0 = s1;
+                    s1 = q;
                 }
                 beg[t] = (short)lo;
                 end[t] = (short)(top + 1);
@@ -172,9 +260,13 @@ __global__ void __launch_bounds__(1024, 1) ct_pass_kernel(CtArgs<T> a)
         __syncthreads();
         // ---- B: pairwise merges ------------------------------------------------
         for (int s = 1; s < G; s <<= 1) {
-            if (active && (t & (2 * s - 1)) == 0 && t + s < G) merge_pair(f, stk, beg, end, t, s, n, hh);
-            __syncthreads();
+            if (active && (t & (2 * s - 1)) == 0 && t + s < G) merge_pair<K>(f, stk, beg, end, t, s, n, hh);
+            // the next level merges groups of 4s threads: inside one warp, a warp
+            // barrier publishes this level's segment updates; otherwise a CTA barrier
+            if (4 * s <= 32) __syncwarp();
+            else __syncthreads();
         }
+        __syncthreads();
         // ---- C: compaction -------------------------------------------------------
         const int cnt = active ? (end[t] - beg[t]) : 0;
         int incl = cnt;
@@ -195,7 +287,7 @@ __global__ void __launch_bounds__(1024, 1) ct_pass_kernel(CtArgs<T> a)
         if (active) {
             const int b0 = beg[t];
             const int excl = incl - cnt;
-            for (int i = 0; i < cnt; ++i) hull[excl + i] = stk[b0 + i];
+            for (int i = 0; i < cnt; ++i) hull[excl + i] = stk[SK::s(b0 + i)];
         }
         __syncthreads();
         // ---- D: evaluate this thread's outputs -----------------------------------
@@ -206,12 +298,12 @@ __global__ void __launch_bounds__(1024, 1) ct_pass_kernel(CtArgs<T> a)
             while (kl < kh) {
                 const int mid = (kl + kh) >> 1;
                 const int j0 = hull[mid], j1 = hull[mid + 1];
-                if (parab(hh, lo, j1, f[j1]) < parab(hh, lo, j0, f[j0])) kl = mid + 1;
+                if (parab(hh, lo, j1, f[SK::f(j1)]) < parab(hh, lo, j0, f[SK::f(j0)])) kl = mid + 1;
                 else kh = mid;
             }
             int k = kl;
             int jc = hull[k];
-            T fc = f[jc];
+            T fc = f[SK::f(jc)];
 #pragma unroll
             for (int q = 0; q < K; ++q) {
                 const int x = lo + q;
@@ -219,7 +311,7 @@ __global__ void __launch_bounds__(1024, 1) ct_pass_kernel(CtArgs<T> a)
                     T vc = parab(hh, x, jc, fc);
                     while (k + 1 < H) {
                         const int jn = hull[k + 1];
-                        const T fn = f[jn];
+                        const T fn = f[SK::f(jn)];
                         const T vn = parab(hh, x, jn, fn);
                         if (vn <= vc) { ++k; jc = jn; fc = fn; vc = vn; }
                         else break;
@@ -232,19 +324,49 @@ __global__ void __launch_bounds__(1024, 1) ct_pass_kernel(CtArgs<T> a)
         if (active && lo < n) {
 #pragma unroll
             for (int q = 0; q < K; ++q)
-                if (lo + q < hi) f[lo + q] = outv[q];
+                if (lo + q < hi) f[SK::f(lo + q)] = outv[q];
         }
         __syncthreads();
         // ---- store ---------------------------------------------------------------
-        for (int e = tid; e < total; e += blockDim.x) {
-            int ww, p;
-            if (CONTIG) { ww = e / n; p = e - ww * n; }
-            else        { p = e / tl.wact; ww = e - p * tl.wact; }
-            const long long ad = addr_of(lt, tl, ww, p);
-            const T v = fs[(size_t)ww * a.LD + p];
-            a.out[ad] = v;
-            if (a.w_out) acc_out += (double)v * (double)a.w_out[ad];
+        if (CONTIG) {
+            for (int ww = 0; ww < tl.wact; ++ww) {
+                const long long rb = tl.base0 + (long long)ww * n;
+                const T* frow = fs + (size_t)ww * a.LD;
+                if (sizeof(T) == 4 && a.vec4) {
+                    float4* dst = reinterpret_cast<float4*>(a.out + rb);
+                    const float4* wsrc = reinterpret_cast<const float4*>(a.w_out + rb);
+                    for (int q = tid; q < (n >> 2); q += blockDim.x) {
+                        const float4 v = make_float4(frow[SK::f(4 * q)], frow[SK::f(4 * q + 1)],
+                                                     frow[SK::f(4 * q + 2)], frow[SK::f(4 * q + 3)]);
+                        dst[q] = v;
+                        if (a.w_out) {
+                            const float4 u = wsrc[q];
+                            acc_t_out.add_prod(v.x, u.x); acc_t_out.add_prod(v.y, u.y);
+                            acc_t_out.add_prod(v.z, u.z); acc_t_out.add_prod(v.w, u.w);
+                        }
+                    }
+                } else {
+                    for (int p = tid; p < n; p += blockDim.x) {
+                        const T v = frow[SK::f(p)];
+                        a.out[rb + p] = v;
+                        if (a.w_out) acc_t_out.add_prod(v, a.w_out[rb + p]);
+                    }
+                }
+            }
+        } else {
+            const int total = n << a.lw;
+            for (int e = tid; e < total; e += blockDim.x) {
+                const int p = e >> a.lw, ww = e & (W - 1);
+                if (ww < tl.wact) {
+                    const long long ad = tl.base0 + ww + (long long)p * lt.es;
+                    const T v = fs[(size_t)ww * a.LD + SK::f(p)];
+                    a.out[ad] = v;
+                    if (a.w_out) acc_t_out.add_prod(v, a.w_out[ad]);
+                }
+            }
         }
+        acc_in += acc_t_in.take();
+        acc_out += acc_t_out.take();
         __syncthreads();
     }
     if (a.part_in) {
@@ -320,21 +442,29 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
     p.K = pick_K(n);
     p.G = next_pow2((n + p.K - 1) / p.K);
     const bool contig = (axis == 0);
-    const int LDI = n + (n & 1) + 8;
+    const int chunks = (n + p.K - 1) / p.K + 1;
+    const int LDI = n + 2 * chunks + (n & 1) + 8;        // skewed index stack (two shorts per chunk)
+    const int nf = n + chunks + 1;                        // skewed values (one word per chunk)
     // lines per CTA: at most 1024 threads, at most 32 lines, a shared-memory budget
-    const size_t line_bytes = (size_t)(n + 32) * elem_bytes + 2 * (size_t)LDI * 2 + 2 * (size_t)p.G * 2 + 64;
-    int W = 1024 / p.G;
+    const size_t line_bytes = (size_t)(nf + 32) * elem_bytes + 2 * (size_t)LDI * 2 + 2 * (size_t)p.G * 2 + 64;
+    // up to 512 threads per CTA so that two CTAs share an SM
+    int W = 512 / p.G;
     if (W < 1) W = 1;
     if (W > 32) W = 32;
-    const size_t budget = 200 * 1024;
+    const size_t budget = 110 * 1024;                      // two CTAs per SM
     while (W > 1 && (size_t)W * line_bytes > budget) --W;
-    if (!contig && W > g.n[0]) W = g.n[0];
+    if (!contig) {
+        // interleaved tiles: W a power of two (division-free index math)
+        int p2 = 1;
+        while (p2 * 2 <= W) p2 *= 2;
+        W = p2;
+    }
     // leading dimension: for interleaved loads consecutive lanes hit the W lines
     // of one position; pick the stride with the fewest shared-memory bank conflicts
-    int LD = n;
+    int LD = nf;
     if (!contig) {
         int best = 1 << 30;
-        for (int cand = n; cand <= n + 32; ++cand) {
+        for (int cand = nf; cand <= nf + 32; ++cand) {
             const int c = bank_conflicts(cand, W, elem_bytes / 4);
             if (c < best) { best = c; LD = cand; }
         }
@@ -363,6 +493,10 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
     const double h = 1.0 / g.n[axis];
     a.hh = (T)(0.5 * h * h);
     a.negate = negate ? 1 : 0;
+    auto al16 = [](const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    a.vec4 = (axis == 0 && g.n[0] % 4 == 0 && al16(in) && al16(out) && al16(w_in) && al16(w_out)) ? 1 : 0;
+    a.lw = 0;
+    while ((1 << a.lw) < p.W) ++a.lw;
     void* k = select_kernel<T>(p.K, axis == 0);
     BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     long long blocks = p.tiles.ntiles;

@@ -38,16 +38,24 @@ struct DctArgs {
     const cx_t<T>* tw;        // e^{-2 pi i j/n}
     const cx_t<T>* dtw;       // e^{-i pi k/(2n)}
     const unsigned short* drev;   // digit reversal of the stage radices
-    const double* lam_axis;   // MID: eigenvalues along this axis
-    const double* lam_a0;     // MID: eigenvalues along axis 0 (index of the line)
-    const double* lam_a1;     // MID (3D): eigenvalues along axis 1 (outer index)
+    const T* lam_axis;        // MID: eigenvalues along this axis
+    const T* lam_a0;          // MID: eigenvalues along axis 0 (index of the line)
+    const T* lam_a1;          // MID (3D): eigenvalues along axis 1 (outer index)
     LineTiles lt;
     int G;                    // threads per line pair
     int LDZ;                  // shared leading dimension (complex elements)
     int nst;
     int rad[kMaxStages];
+    int Ls[kMaxStages];       // sub-transform length entering stage s (product of earlier radices)
+    unsigned mag[kMaxStages]; // ceil(2^32 / Ls[s]): b / Ls[s] = umulhi(b, mag[s]) for b < n
+    int lnp;                  // log2(pairs per tile) for interleaved tiles
     double gscale;            // MID: 1 / N^2
 };
+
+__device__ __forceinline__ int div_by(int b, int L, unsigned mag)
+{
+    return L == 1 ? b : (int)__umulhi((unsigned)b, mag);
+}
 
 // r-point DFT, SIGN = -1 forward, +1 inverse
 template <int SIGN, typename C>
@@ -98,45 +106,55 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1) dct_pass_kerne
     T sig = (T)0;
     if (MODE == DCT_INV && a.upd) sig = (T)(*a.sigma);
     double acc = 0.0;
+    Acc<T> gsum;
 
     for (long long tile = blockIdx.x; tile < lt.ntiles; tile += gridDim.x) {
         const Tile tl = tile_at(lt, tile);
         const int np = (tl.wact + 1) / 2;
-        const int total = np * n;
         // ---- load ------------------------------------------------------------
-        for (int e = tid; e < total; e += blockDim.x) {
-            int q, j;
-            if (CONTIG) { q = e / n; j = e - q * n; }
-            else        { j = e / np; q = e - j * np; }
-            const int la = 2 * q, lb = 2 * q + 1;
-            const long long ada = addr_of(lt, tl, la, j);
-            T xa = a.in[ada];
-            T xb = (T)0;
-            if (lb < tl.wact) xb = a.in[ada + tl.lstride];
-            if (MODE == DCT_FWD && a.base) {
-                xa = a.base[ada] - xa;
-                if (lb < tl.wact) xb = a.base[ada + tl.lstride] - xb;
-            }
-            C v; v.x = xa; v.y = xb;
-            if (MODE == DCT_INV) {
-                zs[(size_t)q * a.LDZ + j] = v;                       // natural order
-            } else {
-                const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
-                zs[(size_t)q * a.LDZ + a.drev[m]] = v;               // DIT input order
+        {
+            // CONTIG: one row pair after another; interleaved: pairs fastest
+            const int np_pow = CONTIG ? 1 : (1 << a.lnp);
+            const int per = CONTIG ? n : np_pow * n;
+            const int reps = CONTIG ? np : 1;
+            for (int q0 = 0; q0 < reps; ++q0)
+            for (int e = tid; e < per; e += blockDim.x) {
+                int q, j;
+                if (CONTIG) { q = q0; j = e; }
+                else        { q = e & (np_pow - 1); j = e >> a.lnp; }
+                if (q >= np) continue;
+                const int lb = 2 * q + 1;
+                const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                T xa = a.in[ada];
+                T xb = (T)0;
+                if (lb < tl.wact) xb = a.in[ada + tl.lstride];
+                if (MODE == DCT_FWD && a.base) {
+                    xa = a.base[ada] - xa;
+                    if (lb < tl.wact) xb = a.base[ada + tl.lstride] - xb;
+                }
+                C v; v.x = xa; v.y = xb;
+                if (MODE == DCT_INV) {
+                    zs[(size_t)q * a.LDZ + j] = v;                       // natural order
+                } else {
+                    const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
+                    zs[(size_t)q * a.LDZ + a.drev[m]] = v;               // DIT input order
+                }
             }
         }
         __syncthreads();
         const bool active = (pp < np);
         if (MODE != DCT_INV) {
             // ---- forward DIT FFT ---------------------------------------------
-            int L = 1;
             for (int s = 0; s < a.nst; ++s) {
                 const int r = a.rad[s];
+                const int L = a.Ls[s];
                 const int Lp = L * r;
-                const int tstep = n / Lp;
+                const int tstep = (s + 1 < a.nst) ? n / Lp : 1;
+                const unsigned mg = a.mag[s];
+                const int nb = (r == 4) ? (n >> 2) : (r == 2 ? (n >> 1) : n / 3);
                 if (active) {
-                    for (int b = t; b < n / r; b += G) {
-                        const int B = b / L, k1 = b - B * L;
+                    for (int b = t; b < nb; b += G) {
+                        const int B = div_by(b, L, mg), k1 = b - B * L;
                         const int base = B * Lp + k1;
                         C u[4];
                         for (int q = 0; q < r; ++q) {
@@ -148,7 +166,6 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1) dct_pass_kerne
                         for (int q = 0; q < r; ++q) z[base + q * L] = u[q];
                     }
                 }
-                L = Lp;
                 __syncthreads();
             }
             // ---- separate the two lines, apply e^{-i pi k/2n} -------------------
@@ -179,27 +196,28 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1) dct_pass_kerne
             // ---- divide by the eigenvalues; G = (1/N^2) sum w X^2 / lambda ------------
             if (active) {
                 const int ia = tl.i0 + 2 * pp, ib = ia + 1;
-                double La = a.lam_a0[ia], Lb = (2 * pp + 1 < tl.wact) ? a.lam_a0[ib] : 0.0;
-                double wa = (ia == 0) ? 1.0 : 2.0, wb = (ib == 0) ? 1.0 : 2.0;
+                const bool has_b = (2 * pp + 1 < tl.wact);
+                T La = a.lam_a0[ia], Lb = has_b ? a.lam_a0[ib] : (T)0;
+                T wa = (ia == 0) ? (T)1 : (T)2, wb = (ib == 0) ? (T)1 : (T)2;
                 if (a.lam_a1) {
                     const int jo = (int)tl.outer;
                     La += a.lam_a1[jo]; Lb += a.lam_a1[jo];
-                    const double wo = (jo == 0) ? 1.0 : 2.0;
+                    const T wo = (jo == 0) ? (T)1 : (T)2;
                     wa *= wo; wb *= wo;
                 }
-                const bool has_b = (2 * pp + 1 < tl.wact);
                 for (int k = t; k < n; k += G) {
-                    const double lk = a.lam_axis[k];
-                    const double wk = (k == 0) ? 1.0 : 2.0;
+                    const T lk = a.lam_axis[k];
+                    const T wk = (k == 0) ? (T)1 : (T)2;
                     C v = z[k];
-                    const double la = La + lk, lb = Lb + lk;
-                    double ga = 0.0, gb = 0.0;
-                    if (la > 0.0) { ga = (double)v.x / la; acc += wa * wk * (double)v.x * ga; }
-                    if (has_b && lb > 0.0) { gb = (double)v.y / lb; acc += wb * wk * (double)v.y * gb; }
-                    v.x = (T)ga; v.y = (T)gb;
+                    const T la = La + lk, lb = Lb + lk;
+                    T ga = (T)0, gb = (T)0;
+                    if (la > (T)0) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
+                    if (has_b && lb > (T)0) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
+                    v.x = ga; v.y = gb;
                     z[k] = v;
                 }
             }
+            acc += gsum.take();
             __syncthreads();
         }
         if (MODE != DCT_FWD) {
@@ -228,17 +246,16 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1) dct_pass_kerne
             }
             __syncthreads();
             // ---- inverse DIF FFT -----------------------------------------------------
-            int Lend = 1;
-            for (int s = 0; s < a.nst; ++s) Lend *= a.rad[s];
-            int L = Lend;
             for (int s = a.nst - 1; s >= 0; --s) {
                 const int r = a.rad[s];
-                const int Lp = L;
-                L = Lp / r;
-                const int tstep = n / Lp;
+                const int L = a.Ls[s];
+                const int Lp = L * r;
+                const int tstep = (s + 1 < a.nst) ? n / Lp : 1;
+                const unsigned mg = a.mag[s];
+                const int nb = (r == 4) ? (n >> 2) : (r == 2 ? (n >> 1) : n / 3);
                 if (active) {
-                    for (int b = t; b < n / r; b += G) {
-                        const int B = b / L, k1 = b - B * L;
+                    for (int b = t; b < nb; b += G) {
+                        const int B = div_by(b, L, mg), k1 = b - B * L;
                         const int base = B * Lp + k1;
                         C u[4];
                         for (int q = 0; q < r; ++q) u[q] = z[base + q * L];
@@ -254,27 +271,34 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1) dct_pass_kerne
             }
         }
         // ---- store ------------------------------------------------------------------
-        for (int e = tid; e < total; e += blockDim.x) {
-            int q, j;
-            if (CONTIG) { q = e / n; j = e - q * n; }
-            else        { j = e / np; q = e - j * np; }
-            const int la = 2 * q, lb = 2 * q + 1;
-            const long long ada = addr_of(lt, tl, la, j);
-            C v;
-            if (MODE == DCT_FWD) {
-                v = zs[(size_t)q * a.LDZ + j];
-            } else {
-                const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
-                v = zs[(size_t)q * a.LDZ + a.drev[m]];
-                v.x *= inv_n;
-                v.y *= inv_n;
-            }
-            if (MODE == DCT_INV && a.upd) {
-                a.out[ada] = a.upd[ada] + sig * v.x;
-                if (lb < tl.wact) a.out[ada + tl.lstride] = a.upd[ada + tl.lstride] + sig * v.y;
-            } else {
-                a.out[ada] = v.x;
-                if (lb < tl.wact) a.out[ada + tl.lstride] = v.y;
+        {
+            const int np_pow = CONTIG ? 1 : (1 << a.lnp);
+            const int per = CONTIG ? n : np_pow * n;
+            const int reps = CONTIG ? np : 1;
+            for (int q0 = 0; q0 < reps; ++q0)
+            for (int e = tid; e < per; e += blockDim.x) {
+                int q, j;
+                if (CONTIG) { q = q0; j = e; }
+                else        { q = e & (np_pow - 1); j = e >> a.lnp; }
+                if (q >= np) continue;
+                const int lb = 2 * q + 1;
+                const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                C v;
+                if (MODE == DCT_FWD) {
+                    v = zs[(size_t)q * a.LDZ + j];
+                } else {
+                    const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
+                    v = zs[(size_t)q * a.LDZ + a.drev[m]];
+                    v.x *= inv_n;
+                    v.y *= inv_n;
+                }
+                if (MODE == DCT_INV && a.upd) {
+                    a.out[ada] = a.upd[ada] + sig * v.x;
+                    if (lb < tl.wact) a.out[ada + tl.lstride] = a.upd[ada + tl.lstride] + sig * v.y;
+                } else {
+                    a.out[ada] = v.x;
+                    if (lb < tl.wact) a.out[ada + tl.lstride] = v.y;
+                }
             }
         }
         __syncthreads();
@@ -291,7 +315,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1) dct_pass_kerne
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void fill_tables_kernel(int n, cx_t<T>* tw, cx_t<T>* dtw, unsigned short* drev,
-                                   double* lam, int nst, FftRadices rs)
+                                   T* lam, int nst, FftRadices rs)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -301,7 +325,7 @@ __global__ void fill_tables_kernel(int n, cx_t<T>* tw, cx_t<T>* dtw, unsigned sh
     sincospi(-(double)j / (2.0 * (double)n), &s, &c);
     dtw[j].x = (T)c; dtw[j].y = (T)s;
     const double sh = sinpi((double)j / (2.0 * (double)n));
-    lam[j] = 4.0 * (double)n * (double)n * sh * sh;
+    lam[j] = (T)(4.0 * (double)n * (double)n * sh * sh);
     // digit reversal: element m -> position p (DIT with radices rs.r[0..nst))
     int m = j, p = 0, Lw[kMaxStages];
     int L = 1;
@@ -347,7 +371,7 @@ bool layout_axis_tables(int n, int elem_bytes, unsigned char* ws, AxisTables* t)
     t->tw = ws;
     t->dtw = ws + cb;
     t->drev = reinterpret_cast<unsigned short*>(ws + 2 * cb);
-    t->lam = reinterpret_cast<double*>(ws + 2 * cb + up((size_t)n * 2));
+    t->lam = ws + 2 * cb + up((size_t)n * 2);
     return true;
 }
 
@@ -356,8 +380,8 @@ bfm_status fill_axis_tables(int n, AxisTables* t, unsigned char* ws, cudaStream_
 {
     if (!layout_axis_tables(n, (int)sizeof(T), ws, t)) return BFM_ERR_UNSUPPORTED;
     fill_tables_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(
-        n, reinterpret_cast<cx_t<T>*>(t->tw), reinterpret_cast<cx_t<T>*>(t->dtw), t->drev, t->lam,
-        t->rs.nst, t->rs);
+        n, reinterpret_cast<cx_t<T>*>(t->tw), reinterpret_cast<cx_t<T>*>(t->dtw), t->drev,
+        reinterpret_cast<T*>(t->lam), t->rs.nst, t->rs);
     BFM_LAUNCH_CHECK("fill_tables_kernel");
     return BFM_OK;
 }
@@ -385,7 +409,12 @@ DctPlan plan_dct_pass(const Grid& g, int axis, int elem_bytes)
     int W = 2 * (max_threads / G);
     while (W > 2 && (size_t)(W / 2) * pair_bytes > budget) W -= 2;
     if (W > 32) W = 32;
-    if (!contig && W > g.n[0]) W = g.n[0];
+    if (!contig) {
+        if (W > g.n[0]) W = g.n[0];
+        int p2 = 1;                       // power of two: division-free index math
+        while (p2 * 2 <= W) p2 *= 2;
+        W = p2;
+    }
     if (W < 1) W = 1;
     p.W = W;
     const int npairs = (W + 1) / 2;
@@ -421,14 +450,27 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
     a.tw = reinterpret_cast<const cx_t<T>*>(tb.tw);
     a.dtw = reinterpret_cast<const cx_t<T>*>(tb.dtw);
     a.drev = tb.drev;
-    a.lam_axis = tb.lam;
-    a.lam_a0 = tabs[0].lam;
-    a.lam_a1 = (g.ndim == 3) ? tabs[1].lam : nullptr;
+    a.lam_axis = reinterpret_cast<const T*>(tb.lam);
+    a.lam_a0 = reinterpret_cast<const T*>(tabs[0].lam);
+    a.lam_a1 = (g.ndim == 3) ? reinterpret_cast<const T*>(tabs[1].lam) : nullptr;
     a.lt = p.tiles;
     a.G = p.G;
     a.LDZ = p.LDZ;
     a.nst = tb.rs.nst;
-    for (int i = 0; i < kMaxStages; ++i) a.rad[i] = (i < tb.rs.nst) ? tb.rs.r[i] : 0;
+    {
+        int L = 1;
+        for (int i = 0; i < kMaxStages; ++i) {
+            a.rad[i] = (i < tb.rs.nst) ? tb.rs.r[i] : 0;
+            a.Ls[i] = L;
+            a.mag[i] = (L > 1) ? (unsigned)((((unsigned long long)1 << 32) + L - 1) / L) : 0u;
+            if (i < tb.rs.nst) L *= tb.rs.r[i];
+        }
+    }
+    {
+        const int npt = (p.W + 1) / 2;
+        a.lnp = 0;
+        while ((1 << a.lnp) < npt) ++a.lnp;
+    }
     a.gscale = 1.0 / ((double)g.N * (double)g.N);
     void* k;
     const bool contig = (axis == 0);

@@ -22,7 +22,7 @@ struct AxisTables {
     void* tw;                 // complex, n
     void* dtw;                // complex, n
     unsigned short* drev;     // n
-    double* lam;              // n
+    void* lam;                // n, element type of the call
 };
 
 struct DctPlan {
