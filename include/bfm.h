@@ -174,6 +174,45 @@ const char *bfm_profile_kind_name(int kind);
 bfm_status bfm_profile_begin(int max_records);
 bfm_status bfm_profile_end(double *ms_by_kind, int *launches_by_kind, int nkinds, int *dropped);
 
+/*
+ * Many independent problems of uneven sizes (Algorithm 1 on each, as in
+ * bfm_solve), solved together: problem p has grid grids[p], DEVICE inputs
+ * mu[p], nu[p] and the outputs/logs of outs[p] (see bfm_result).  Each problem
+ * keeps its own step size, logs and convergence flag; a problem that has
+ * converged (or reached max_iter) does no further work while the others
+ * continue.  Problems of equal grid shape share each kernel launch; a chunk of
+ * opt->poll_every iterations is captured once as a CUDA graph and replayed
+ * until every problem has stopped.  Returns BFM_OK when all converged,
+ * BFM_NOT_CONVERGED when some reached max_iter (outs[p].converged says which).
+ * opt->warm_start is not supported here.  Synchronises `stream`.
+ */
+size_t bfm_workspace_bytes_batched(int nprob, const bfm_grid *grids, bfm_precision prec,
+                                   int max_iter);
+bfm_status bfm_solve_batched(int nprob, const void *const *mu, const void *const *nu,
+                             const bfm_grid *grids, bfm_cost cost, bfm_precision prec, double tol,
+                             int max_iter, const bfm_options *opt, void *workspace,
+                             size_t workspace_bytes, void *stream, bfm_result *outs);
+
+/*
+ * Backward of the loss W2^2(mu_p, nu_p) for a batch of converged solves.  By
+ * the envelope theorem on the dual problem (eq. (symmetric_dual)) at its
+ * optimum, dC/dnu = phi and dC/dmu = psi, so along mass-preserving
+ * perturbations of the density values
+ *     grad_mu[p] = grad_out[p] * 2 hd (psi[p] - mean psi[p]) / mass_mu[p],
+ *     grad_nu[p] = grad_out[p] * 2 hd (phi[p] - mean phi[p]) / mass_nu[p],
+ * hd = 1/N.  phi, psi: DEVICE potentials from the forward solves (N each);
+ * mass_mu, mass_nu: HOST, the masses bfm_solve reported; grad_out: DEVICE,
+ * nprob elements of the call's precision; grad_mu, grad_nu: DEVICE outputs
+ * (N each), either array (or an entry of it) may be NULL to skip it.
+ * Synchronises `stream`.
+ */
+size_t bfm_w2_backward_workspace_bytes(int nprob);
+bfm_status bfm_w2_backward(int nprob, const bfm_grid *grids, bfm_precision prec,
+                           const void *const *phi, const void *const *psi,
+                           const double *mass_mu, const double *mass_nu, const void *grad_out,
+                           void *const *grad_mu, void *const *grad_nu, void *workspace,
+                           size_t workspace_bytes, void *stream);
+
 /* Workspace bytes for bfm_solve_host: bfm_workspace_bytes plus device room
  * for mu, nu, phi, psi and the map. */
 size_t bfm_workspace_bytes_host(const bfm_grid *grid, bfm_precision prec, int max_iter);

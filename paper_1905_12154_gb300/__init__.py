@@ -10,5 +10,6 @@ from .binding import (  # noqa: F401
     BFM_FP32, BFM_FP64, BFM_OK, BFM_NOT_CONVERGED, BfmError,
     bfm_ctransform, bfm_interpolate, bfm_map, bfm_poisson, bfm_pushforward,
     bfm_solve, bfm_solve_host, bfm_workspace_bytes, bfm_workspace_bytes_host,
-    bfm_poisson_workspace_bytes, status_string, last_error,
+    bfm_poisson_workspace_bytes, status_string, last_error, bfm_solve_batched,
+    bfm_w2_backward, w2_loss, BfmSolver,
 )

@@ -92,6 +92,21 @@ _SIGS = {
                                           ctypes.c_size_t, _P, _P, _P]),
     "bfm_solver_finish": (ctypes.c_int, [_GP, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t,
                                          _P, ctypes.POINTER(bfm_result)]),
+    "bfm_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.c_int, _GP, ctypes.c_int,
+                                                      ctypes.c_int]),
+    "bfm_solve_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_void_p), _GP, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                         ctypes.POINTER(bfm_options), _P, ctypes.c_size_t, _P,
+                                         ctypes.POINTER(bfm_result)]),
+    "bfm_w2_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "bfm_w2_backward": (ctypes.c_int, [ctypes.c_int, _GP, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), _P,
+                                       ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_void_p), _P, ctypes.c_size_t, _P]),
     "bfm_profile_kinds": (ctypes.c_int, []),
     "bfm_profile_kind_name": (ctypes.c_char_p, [ctypes.c_int]),
     "bfm_profile_begin": (ctypes.c_int, [ctypes.c_int]),
@@ -428,3 +443,129 @@ def bfm_profile_end() -> dict:
     out = {lib().bfm_profile_kind_name(i).decode(): (ms[i], cnt[i]) for i in range(k)}
     out["_dropped"] = (0.0, dropped.value)
     return out
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = t.data_ptr() if t is not None else None
+    return arr
+
+
+def bfm_solve_batched(mus, nus, tol: float = 1e-4, max_iter: int = 500, with_map: bool = False,
+                      **opts) -> list:
+    """Independent problems of uneven grid sizes solved together (one batched
+    launch per kernel step and grid shape, per-problem convergence).  `mus`,
+    `nus`: lists of CUDA tensors (same dtype).  Returns one dict per problem."""
+    import torch
+    n = len(mus)
+    if n == 0 or len(nus) != n:
+        raise ValueError("mus and nus must be non-empty lists of equal length")
+    prec = _prec(mus[0])
+    grids = (bfm_grid * n)()
+    results = (bfm_result * n)()
+    keep, logs = [], []
+    for i, (m, v) in enumerate(zip(mus, nus)):
+        _dev(m, "mu"); _dev(v, "nu")
+        if m.shape != v.shape or _prec(m) != prec or _prec(v) != prec:
+            raise ValueError("each mu/nu pair must share shape and dtype")
+        g = grid_of(m.shape)
+        grids[i] = g
+        phi = torch.empty_like(m); psi = torch.empty_like(m)
+        tmap = torch.empty((m.dim(),) + tuple(m.shape), dtype=m.dtype, device=m.device) if with_map else None
+        L = max_iter + 1
+        lg = (np.zeros(L), np.zeros(L), np.zeros(L))
+        r = results[i]
+        r.phi = phi.data_ptr(); r.psi = psi.data_ptr(); r.map = tmap.data_ptr() if with_map else None
+        r.dual = lg[0].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.resid = lg[1].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.sigma = lg[2].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        keep.append((phi, psi, tmap))
+        logs.append(lg)
+    nb = lib().bfm_workspace_bytes_batched(n, grids, prec, max_iter)
+    if nb == 0:
+        raise BfmError(BFM_ERR_INVALID_ARG, "bfm_workspace_bytes_batched")
+    ws_keep, ws = _workspace(nb, mus[0].device)
+    o = _options(**opts)
+    s = lib().bfm_solve_batched(n, _ptr_array(mus), _ptr_array(nus), grids, BFM_COST_QUADRATIC,
+                                prec, float(tol), int(max_iter), ctypes.byref(o), ws, nb,
+                                _stream(), results)
+    _check(s, "bfm_solve_batched", ok=(BFM_OK, BFM_NOT_CONVERGED))
+    out = []
+    for i in range(n):
+        r = results[i]
+        it = r.iters
+        phi, psi, tmap = keep[i]
+        out.append(dict(phi=phi, psi=psi, map=tmap, w2sq=r.w2sq, iters=it,
+                        converged=bool(r.converged), mass_mu=r.mass_mu, mass_nu=r.mass_nu,
+                        max_mu=r.max_mu, max_nu=r.max_nu, dual=logs[i][0][:it + 1].copy(),
+                        resid=logs[i][1][:it + 1].copy(), sigma=logs[i][2][:it + 1].copy()))
+    del ws_keep
+    return out
+
+
+def bfm_w2_backward(phis, psis, mass_mu, mass_nu, grad_out, want_mu: bool = True,
+                    want_nu: bool = True):
+    """Gradients of W2^2 with respect to the density values (envelope theorem):
+    returns (grad_mu list, grad_nu list); grad_out is a CUDA tensor of len(phis)."""
+    import torch
+    n = len(phis)
+    prec = _prec(phis[0])
+    grids = (bfm_grid * n)()
+    for i, p in enumerate(phis):
+        grids[i] = grid_of(p.shape)
+    gmu = [torch.empty_like(p) for p in psis] if want_mu else None
+    gnu = [torch.empty_like(p) for p in phis] if want_nu else None
+    mm = (ctypes.c_double * n)(*[float(x) for x in mass_mu])
+    mn = (ctypes.c_double * n)(*[float(x) for x in mass_nu])
+    go = _dev(grad_out.to(phis[0].dtype).contiguous(), "grad_out")
+    nb = lib().bfm_w2_backward_workspace_bytes(n)
+    ws_keep, ws = _workspace(nb, phis[0].device)
+    s = lib().bfm_w2_backward(n, grids, prec, _ptr_array(phis), _ptr_array(psis), mm, mn,
+                              go.data_ptr(), _ptr_array(gmu) if want_mu else None,
+                              _ptr_array(gnu) if want_nu else None, ws, nb, _stream())
+    _check(s, "bfm_w2_backward")
+    del ws_keep
+    return gmu, gnu
+
+
+def _autograd_function():
+    import torch
+
+    class W2Loss(torch.autograd.Function):
+        """W2^2(mu_b, nu_b) for a batch of density pairs on one grid, shape
+        (B, *grid); the backward kernel returns the mean-zero potentials as the
+        gradients (envelope theorem)."""
+
+        @staticmethod
+        def forward(ctx, mu, nu, tol, max_iter):
+            mus = [m.contiguous() for m in mu.detach()]
+            nus = [v.contiguous() for v in nu.detach()]
+            res = bfm_solve_batched(mus, nus, tol=tol, max_iter=max_iter)
+            ctx.phis = [r["phi"] for r in res]
+            ctx.psis = [r["psi"] for r in res]
+            ctx.mass_mu = [r["mass_mu"] for r in res]
+            ctx.mass_nu = [r["mass_nu"] for r in res]
+            ctx.results = res
+            return torch.tensor([r["w2sq"] for r in res], dtype=mu.dtype, device=mu.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            gmu, gnu = bfm_w2_backward(ctx.phis, ctx.psis, ctx.mass_mu, ctx.mass_nu, grad_out,
+                                       want_mu=ctx.needs_input_grad[0],
+                                       want_nu=ctx.needs_input_grad[1])
+            return (torch.stack(gmu) if gmu is not None else None,
+                    torch.stack(gnu) if gnu is not None else None, None, None)
+
+    return W2Loss
+
+
+_W2 = None
+
+
+def w2_loss(mu, nu, tol: float = 1e-5, max_iter: int = 500):
+    """Differentiable W2^2 between batches of densities mu, nu of shape (B, *grid)."""
+    global _W2
+    if _W2 is None:
+        _W2 = _autograd_function()
+    return _W2.apply(mu, nu, tol, max_iter)

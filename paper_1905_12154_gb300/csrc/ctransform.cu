@@ -22,6 +22,8 @@
 // Optional FP64 dot products of the input and of the output with weight
 // fields (the two terms of the dual value J, eq. (defJ)) are fused into the
 // load and store sweeps and written as one partial sum per CTA.
+#include <string.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -154,9 +156,12 @@ __device__ void merge_pair(const T* f, const short* stk, short* beg, short* end,
     beg[rt] = (short)pc;
 }
 
-template <typename T, int K, bool CONTIG>
-__global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a)
+// BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
+template <typename T, int K, bool CONTIG, bool BATCHED>
+__global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtArgs<T>* batch)
 {
+    const CtArgs<T>& a = BATCHED ? batch[blockIdx.y] : a0;
+    if (BATCHED && blockIdx.x >= a.lt.ntiles) return;
     if (a.done && *a.done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SK = Skew<K>;
@@ -416,20 +421,22 @@ int next_pow2(int x)
 }
 
 template <typename T, int K>
-void* kernel_for(bool contig)
+void* kernel_for(bool contig, bool batched)
 {
-    return contig ? (void*)ct_pass_kernel<T, K, true> : (void*)ct_pass_kernel<T, K, false>;
+    if (batched)
+        return contig ? (void*)ct_pass_kernel<T, K, true, true> : (void*)ct_pass_kernel<T, K, false, true>;
+    return contig ? (void*)ct_pass_kernel<T, K, true, false> : (void*)ct_pass_kernel<T, K, false, false>;
 }
 
 template <typename T>
-void* select_kernel(int K, bool contig)
+void* select_kernel(int K, bool contig, bool batched)
 {
     switch (K) {
-        case 1: return kernel_for<T, 1>(contig);
-        case 2: return kernel_for<T, 2>(contig);
-        case 4: return kernel_for<T, 4>(contig);
-        case 8: return kernel_for<T, 8>(contig);
-        default: return kernel_for<T, 16>(contig);
+        case 1: return kernel_for<T, 1>(contig, batched);
+        case 2: return kernel_for<T, 2>(contig, batched);
+        case 4: return kernel_for<T, 4>(contig, batched);
+        case 8: return kernel_for<T, 8>(contig, batched);
+        default: return kernel_for<T, 16>(contig, batched);
     }
 }
 
@@ -481,11 +488,10 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
 }
 
 template <typename T>
-bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool negate,
-                          const T* w_in, double* part_in, const T* w_out, double* part_out,
-                          const int* done, int max_blocks, cudaStream_t st, int* blocks_used)
+static CtArgs<T> make_ct_args(const Grid& g, int axis, const CtPlan& p, const T* in, T* out,
+                              bool negate, const T* w_in, double* part_in, const T* w_out,
+                              double* part_out, const int* done)
 {
-    CtPlan p = plan_ct_pass(g, axis, (int)sizeof(T));
     CtArgs<T> a;
     a.in = in; a.out = out; a.w_in = w_in; a.w_out = w_out;
     a.part_in = part_in; a.part_out = part_out; a.done = done;
@@ -497,19 +503,82 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
     a.vec4 = (axis == 0 && g.n[0] % 4 == 0 && al16(in) && al16(out) && al16(w_in) && al16(w_out)) ? 1 : 0;
     a.lw = 0;
     while ((1 << a.lw) < p.W) ++a.lw;
-    void* k = select_kernel<T>(p.K, axis == 0);
-    BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    return a;
+}
+
+static int ct_blocks(const CtPlan& p, int max_blocks)
+{
     long long blocks = p.tiles.ntiles;
     const long long cap = (long long)num_sms() * 4;
     if (blocks > cap) blocks = cap;
     if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
-    void* args[] = {&a};
+    return (int)blocks;
+}
+
+template <typename T>
+bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool negate,
+                          const T* w_in, double* part_in, const T* w_out, double* part_out,
+                          const int* done, int max_blocks, cudaStream_t st, int* blocks_used)
+{
+    CtPlan p = plan_ct_pass(g, axis, (int)sizeof(T));
+    CtArgs<T> a = make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out, done);
+    void* k = select_kernel<T>(p.K, axis == 0, false);
+    BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    const int blocks = ct_blocks(p, max_blocks);
+    const CtArgs<T>* none = nullptr;
+    void* args[] = {&a, &none};
     BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(p.threads), args, p.smem, st));
-    if (blocks_used) *blocks_used = (int)blocks;
+    if (blocks_used) *blocks_used = blocks;
     return BFM_OK;
 }
 
+// Batched form: problems that share one grid shape; `dev_args` (device) is
+// filled with one CtArgs per problem by fill_ct_batch_args.
+template <typename T>
+int ct_batch_blocks(const Grid& g, int axis)
+{
+    return ct_blocks(plan_ct_pass(g, axis, (int)sizeof(T)), kMaxPartials);
+}
+
+template <typename T>
+void fill_ct_batch_args(const Grid& g, int axis, const T* in, T* out, bool negate, const T* w_in,
+                        double* part_in, const T* w_out, double* part_out, const int* done,
+                        void* host_slot)
+{
+    CtPlan p = plan_ct_pass(g, axis, (int)sizeof(T));
+    *reinterpret_cast<CtArgs<T>*>(host_slot) =
+        make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out, done);
+}
+
+size_t ct_args_bytes(int elem_bytes) { return elem_bytes == 8 ? sizeof(CtArgs<double>) : sizeof(CtArgs<float>); }
+
+template <typename T>
+bfm_status launch_ct_pass_batched(const Grid& g, int axis, int nprob, const void* dev_args,
+                                  cudaStream_t st)
+{
+    CtPlan p = plan_ct_pass(g, axis, (int)sizeof(T));
+    void* k = select_kernel<T>(p.K, axis == 0, true);
+    BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    const int blocks = ct_blocks(p, kMaxPartials);
+    CtArgs<T> dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    const CtArgs<T>* batch = reinterpret_cast<const CtArgs<T>*>(dev_args);
+    void* args[] = {&dummy, &batch};
+    BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks, (unsigned)nprob), dim3(p.threads), args,
+                              p.smem, st));
+    return BFM_OK;
+}
+
+template int ct_batch_blocks<float>(const Grid&, int);
+template int ct_batch_blocks<double>(const Grid&, int);
+template void fill_ct_batch_args<float>(const Grid&, int, const float*, float*, bool, const float*,
+                                        double*, const float*, double*, const int*, void*);
+template void fill_ct_batch_args<double>(const Grid&, int, const double*, double*, bool,
+                                         const double*, double*, const double*, double*,
+                                         const int*, void*);
+template bfm_status launch_ct_pass_batched<float>(const Grid&, int, int, const void*, cudaStream_t);
+template bfm_status launch_ct_pass_batched<double>(const Grid&, int, int, const void*, cudaStream_t);
 template bfm_status launch_ct_pass<float>(const Grid&, int, const float*, float*, bool, const float*,
                                           double*, const float*, double*, const int*, int,
                                           cudaStream_t, int*);

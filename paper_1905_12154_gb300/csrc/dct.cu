@@ -19,6 +19,8 @@
 //   MID  on the last axis: DCT-II, divide by lambda (zero mode -> 0),
 //        accumulate G = ||g||^2_{H1-dot} in FP64, inverse DCT;
 //   INV  inverse DCT along the axis (optionally out = upd + sigma * g).
+#include <string.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -87,10 +89,14 @@ __device__ __forceinline__ void dft_small(int r, C* u)
     }
 }
 
-template <typename T, int MODE, bool CONTIG>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1) dct_pass_kernel(DctArgs<T> a)
+// BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
+template <typename T, int MODE, bool CONTIG, bool BATCHED>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1)
+dct_pass_kernel(DctArgs<T> a0, const DctArgs<T>* batch)
 {
     using C = cx_t<T>;
+    const DctArgs<T>& a = BATCHED ? batch[blockIdx.y] : a0;
+    if (BATCHED && blockIdx.x >= a.lt.ntiles) return;
     if (a.done && *a.done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* zs = reinterpret_cast<C*>(smem_raw);
@@ -425,9 +431,71 @@ DctPlan plan_dct_pass(const Grid& g, int axis, int elem_bytes)
 }
 
 template <typename T, int MODE>
-static void* dct_kernel(bool contig)
+static void* dct_kernel(bool contig, bool batched)
 {
-    return contig ? (void*)dct_pass_kernel<T, MODE, true> : (void*)dct_pass_kernel<T, MODE, false>;
+    if (batched)
+        return contig ? (void*)dct_pass_kernel<T, MODE, true, true> : (void*)dct_pass_kernel<T, MODE, false, true>;
+    return contig ? (void*)dct_pass_kernel<T, MODE, true, false> : (void*)dct_pass_kernel<T, MODE, false, false>;
+}
+
+template <typename T>
+static bfm_status make_dct_args(const Grid& g, int axis, const DctPlan& p, const AxisTables* tabs,
+                                const T* in, const T* base, T* out, const T* upd,
+                                const double* sigma, double* part, const int* done, DctArgs<T>* a)
+{
+    const AxisTables& tb = tabs[axis];
+    // host-side guard: never launch with tables that do not describe this axis
+    if (tb.n != g.n[axis] || !tb.tw || !tb.dtw || !tb.drev || !tb.lam || tb.rs.nst < 1 ||
+        !tabs[0].lam || (g.ndim == 3 && !tabs[1].lam)) {
+        set_last_error("internal: DCT tables do not match the grid");
+        return BFM_ERR_INVALID_ARG;
+    }
+    a->in = in; a->base = base; a->out = out; a->upd = upd; a->sigma = sigma; a->part = part;
+    a->done = done;
+    a->tw = reinterpret_cast<const cx_t<T>*>(tb.tw);
+    a->dtw = reinterpret_cast<const cx_t<T>*>(tb.dtw);
+    a->drev = tb.drev;
+    a->lam_axis = reinterpret_cast<const T*>(tb.lam);
+    a->lam_a0 = reinterpret_cast<const T*>(tabs[0].lam);
+    a->lam_a1 = (g.ndim == 3) ? reinterpret_cast<const T*>(tabs[1].lam) : nullptr;
+    a->lt = p.tiles;
+    a->G = p.G;
+    a->LDZ = p.LDZ;
+    a->nst = tb.rs.nst;
+    int L = 1;
+    for (int i = 0; i < kMaxStages; ++i) {
+        a->rad[i] = (i < tb.rs.nst) ? tb.rs.r[i] : 0;
+        a->Ls[i] = L;
+        a->mag[i] = (L > 1) ? (unsigned)((((unsigned long long)1 << 32) + L - 1) / L) : 0u;
+        if (i < tb.rs.nst) L *= tb.rs.r[i];
+    }
+    const int npt = (p.W + 1) / 2;
+    a->lnp = 0;
+    while ((1 << a->lnp) < npt) ++a->lnp;
+    a->gscale = 1.0 / ((double)g.N * (double)g.N);
+    return BFM_OK;
+}
+
+static void* select_dct(int mode, int elem_bytes, bool contig, bool batched)
+{
+    if (elem_bytes == 4) {
+        if (mode == DCT_FWD) return dct_kernel<float, DCT_FWD>(contig, batched);
+        if (mode == DCT_MID) return dct_kernel<float, DCT_MID>(contig, batched);
+        return dct_kernel<float, DCT_INV>(contig, batched);
+    }
+    if (mode == DCT_FWD) return dct_kernel<double, DCT_FWD>(contig, batched);
+    if (mode == DCT_MID) return dct_kernel<double, DCT_MID>(contig, batched);
+    return dct_kernel<double, DCT_INV>(contig, batched);
+}
+
+static int dct_blocks(const DctPlan& p)
+{
+    long long blocks = p.tiles.ntiles;
+    const long long cap = (long long)num_sms() * 4;
+    if (blocks > cap) blocks = cap;
+    if (blocks > kMaxPartials) blocks = kMaxPartials;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
 }
 
 template <typename T>
@@ -437,58 +505,61 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
                            cudaStream_t st, int* blocks_used)
 {
     DctPlan p = plan_dct_pass(g, axis, (int)sizeof(T));
-    const AxisTables& tb = tabs[axis];
-    // host-side guard: never launch with tables that do not describe this axis
-    if (tb.n != g.n[axis] || !tb.tw || !tb.dtw || !tb.drev || !tb.lam || tb.rs.nst < 1 ||
-        !tabs[0].lam || (g.ndim == 3 && !tabs[1].lam)) {
-        set_last_error("internal: DCT tables do not match the grid");
-        return BFM_ERR_INVALID_ARG;
-    }
     DctArgs<T> a;
-    a.in = in; a.base = base; a.out = out; a.upd = upd; a.sigma = sigma; a.part = part;
-    a.done = done;
-    a.tw = reinterpret_cast<const cx_t<T>*>(tb.tw);
-    a.dtw = reinterpret_cast<const cx_t<T>*>(tb.dtw);
-    a.drev = tb.drev;
-    a.lam_axis = reinterpret_cast<const T*>(tb.lam);
-    a.lam_a0 = reinterpret_cast<const T*>(tabs[0].lam);
-    a.lam_a1 = (g.ndim == 3) ? reinterpret_cast<const T*>(tabs[1].lam) : nullptr;
-    a.lt = p.tiles;
-    a.G = p.G;
-    a.LDZ = p.LDZ;
-    a.nst = tb.rs.nst;
-    {
-        int L = 1;
-        for (int i = 0; i < kMaxStages; ++i) {
-            a.rad[i] = (i < tb.rs.nst) ? tb.rs.r[i] : 0;
-            a.Ls[i] = L;
-            a.mag[i] = (L > 1) ? (unsigned)((((unsigned long long)1 << 32) + L - 1) / L) : 0u;
-            if (i < tb.rs.nst) L *= tb.rs.r[i];
-        }
-    }
-    {
-        const int npt = (p.W + 1) / 2;
-        a.lnp = 0;
-        while ((1 << a.lnp) < npt) ++a.lnp;
-    }
-    a.gscale = 1.0 / ((double)g.N * (double)g.N);
-    void* k;
-    const bool contig = (axis == 0);
-    if (mode == DCT_FWD) k = dct_kernel<T, DCT_FWD>(contig);
-    else if (mode == DCT_MID) k = dct_kernel<T, DCT_MID>(contig);
-    else k = dct_kernel<T, DCT_INV>(contig);
+    bfm_status s = make_dct_args<T>(g, axis, p, tabs, in, base, out, upd, sigma, part, done, &a);
+    if (s != BFM_OK) return s;
+    void* k = select_dct(mode, (int)sizeof(T), axis == 0, false);
     BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
-    long long blocks = p.tiles.ntiles;
-    const long long cap = (long long)num_sms() * 4;
-    if (blocks > cap) blocks = cap;
-    if (blocks > kMaxPartials) blocks = kMaxPartials;
-    if (blocks < 1) blocks = 1;
-    void* args[] = {&a};
+    const int blocks = dct_blocks(p);
+    const DctArgs<T>* none = nullptr;
+    void* args[] = {&a, &none};
     BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(p.threads), args, p.smem, st));
-    if (blocks_used) *blocks_used = (int)blocks;
+    if (blocks_used) *blocks_used = blocks;
     return BFM_OK;
 }
 
+template <typename T>
+int dct_batch_blocks(const Grid& g, int axis) { return dct_blocks(plan_dct_pass(g, axis, (int)sizeof(T))); }
+
+size_t dct_args_bytes(int elem_bytes) { return elem_bytes == 8 ? sizeof(DctArgs<double>) : sizeof(DctArgs<float>); }
+
+template <typename T>
+bfm_status fill_dct_batch_args(const Grid& g, int axis, const AxisTables* tabs, const T* in,
+                               const T* base, T* out, const T* upd, const double* sigma,
+                               double* part, const int* done, void* host_slot)
+{
+    DctPlan p = plan_dct_pass(g, axis, (int)sizeof(T));
+    return make_dct_args<T>(g, axis, p, tabs, in, base, out, upd, sigma, part, done,
+                            reinterpret_cast<DctArgs<T>*>(host_slot));
+}
+
+template <typename T>
+bfm_status launch_dct_pass_batched(const Grid& g, int axis, int mode, int nprob,
+                                   const void* dev_args, cudaStream_t st)
+{
+    DctPlan p = plan_dct_pass(g, axis, (int)sizeof(T));
+    void* k = select_dct(mode, (int)sizeof(T), axis == 0, true);
+    BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    const int blocks = dct_blocks(p);
+    DctArgs<T> dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    const DctArgs<T>* batch = reinterpret_cast<const DctArgs<T>*>(dev_args);
+    void* args[] = {&dummy, &batch};
+    BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks, (unsigned)nprob), dim3(p.threads), args,
+                              p.smem, st));
+    return BFM_OK;
+}
+
+template int dct_batch_blocks<float>(const Grid&, int);
+template int dct_batch_blocks<double>(const Grid&, int);
+template bfm_status fill_dct_batch_args<float>(const Grid&, int, const AxisTables*, const float*,
+                                               const float*, float*, const float*, const double*,
+                                               double*, const int*, void*);
+template bfm_status fill_dct_batch_args<double>(const Grid&, int, const AxisTables*, const double*,
+                                                const double*, double*, const double*,
+                                                const double*, double*, const int*, void*);
+template bfm_status launch_dct_pass_batched<float>(const Grid&, int, int, int, const void*, cudaStream_t);
+template bfm_status launch_dct_pass_batched<double>(const Grid&, int, int, int, const void*, cudaStream_t);
 template bfm_status launch_dct_pass<float>(const Grid&, int, int, const AxisTables*, const float*,
                                            const float*, float*, const float*, const double*,
                                            double*, const int*, cudaStream_t, int*);

@@ -66,6 +66,34 @@ template <typename T>
 bfm_status launch_interpolate(const Grid& g, const T* map, const T* mu, double t, T* rho,
                               cudaStream_t st);
 
+// batched forms: one launch per kernel step for a class of problems sharing a
+// grid shape; per-problem arguments live in a device array (blockIdx.y)
+template <typename T> int ct_batch_blocks(const Grid& g, int axis);
+size_t ct_args_bytes(int elem_bytes);
+template <typename T>
+void fill_ct_batch_args(const Grid& g, int axis, const T* in, T* out, bool negate, const T* w_in,
+                        double* part_in, const T* w_out, double* part_out, const int* done,
+                        void* host_slot);
+template <typename T>
+bfm_status launch_ct_pass_batched(const Grid& g, int axis, int nprob, const void* dev_args,
+                                  cudaStream_t st);
+template <typename T> int dct_batch_blocks(const Grid& g, int axis);
+size_t dct_args_bytes(int elem_bytes);
+template <typename T>
+bfm_status fill_dct_batch_args(const Grid& g, int axis, const AxisTables* tabs, const T* in,
+                               const T* base, T* out, const T* upd, const double* sigma,
+                               double* part, const int* done, void* host_slot);
+template <typename T>
+bfm_status launch_dct_pass_batched(const Grid& g, int axis, int mode, int nprob,
+                                   const void* dev_args, cudaStream_t st);
+size_t push_args_bytes(int elem_bytes);
+template <typename T>
+void fill_push_batch_args(const Grid& g, const T* psi, const T* mu, T* rho, const int* done,
+                          void* host_slot);
+template <typename T>
+bfm_status launch_pushforward_batched(int ndim, long long max_cells, int nprob,
+                                      const void* dev_args, cudaStream_t st);
+
 // solver.cu: the Poisson solve on an explicit scratch block
 size_t poisson_scratch_bytes(const Grid& g, int eb);
 bfm_status poisson_on_scratch(const void* f, void* g_out, const Grid& g, bfm_precision prec,

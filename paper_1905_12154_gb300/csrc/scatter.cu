@@ -28,6 +28,15 @@ static GridDev dev_grid(const Grid& g)
     return d;
 }
 
+static int grid_blocks(long long N, int threads)
+{
+    long long b = (N + threads - 1) / threads;
+    const long long cap = (long long)num_sms() * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
 // position of T(x) along one axis, in cell-index units, clamped to [0, n-1]
 template <typename T>
 __device__ __forceinline__ T map_pos(const T* psi, long long idx, int i, int n, long long s)
@@ -90,6 +99,75 @@ __global__ void pushforward_kernel(const T* __restrict__ psi, const T* __restric
     }
 }
 
+// Batched pushforward: blockIdx.y selects the problem.
+template <typename T>
+struct PushArgs {
+    const T* psi;
+    const T* mu;
+    T* rho;
+    const int* done;
+    GridDev g;
+};
+
+template <typename T>
+__global__ void zero_batched_kernel(const PushArgs<T>* batch)
+{
+    const PushArgs<T>& a = batch[blockIdx.y];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.g.N; i += stride)
+        a.rho[i] = (T)0;
+}
+
+template <typename T, int NDIM>
+__global__ void pushforward_batched_kernel(const PushArgs<T>* batch)
+{
+    const PushArgs<T>& a = batch[blockIdx.y];
+    if (a.done && *a.done) return;
+    const GridDev& g = a.g;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
+        const T m = a.mu[idx];
+        if (m == (T)0) continue;
+        long long r = idx;
+        T pos[3];
+#pragma unroll
+        for (int ax = 0; ax < NDIM; ++ax) {
+            const int i = (int)(r % g.n[ax]);
+            r /= g.n[ax];
+            pos[ax] = map_pos(a.psi, idx, i, g.n[ax], g.s[ax]);
+        }
+        deposit<T, NDIM>(a.rho, g, pos, m);
+    }
+}
+
+size_t push_args_bytes(int elem_bytes) { return elem_bytes == 8 ? sizeof(PushArgs<double>) : sizeof(PushArgs<float>); }
+
+template <typename T>
+void fill_push_batch_args(const Grid& g, const T* psi, const T* mu, T* rho, const int* done, void* host_slot)
+{
+    PushArgs<T>* a = reinterpret_cast<PushArgs<T>*>(host_slot);
+    a->psi = psi; a->mu = mu; a->rho = rho; a->done = done; a->g = dev_grid(g);
+}
+
+template <typename T>
+bfm_status launch_pushforward_batched(int ndim, long long max_cells, int nprob, const void* dev_args,
+                                      cudaStream_t st)
+{
+    const int th = 256, bl = grid_blocks(max_cells, th);
+    const PushArgs<T>* b = reinterpret_cast<const PushArgs<T>*>(dev_args);
+    zero_batched_kernel<T><<<dim3(bl, nprob), th, 0, st>>>(b);
+    BFM_LAUNCH_CHECK("zero_batched_kernel");
+    if (ndim == 2) pushforward_batched_kernel<T, 2><<<dim3(bl, nprob), th, 0, st>>>(b);
+    else           pushforward_batched_kernel<T, 3><<<dim3(bl, nprob), th, 0, st>>>(b);
+    BFM_LAUNCH_CHECK("pushforward_batched_kernel");
+    return BFM_OK;
+}
+
+template void fill_push_batch_args<float>(const Grid&, const float*, const float*, float*, const int*, void*);
+template void fill_push_batch_args<double>(const Grid&, const double*, const double*, double*, const int*, void*);
+template bfm_status launch_pushforward_batched<float>(int, long long, int, const void*, cudaStream_t);
+template bfm_status launch_pushforward_batched<double>(int, long long, int, const void*, cudaStream_t);
+
 template <typename T, int NDIM>
 __global__ void map_kernel(const T* __restrict__ psi, T* __restrict__ out, GridDev g)
 {
@@ -127,15 +205,6 @@ __global__ void interpolate_kernel(const T* __restrict__ map, const T* __restric
         }
         deposit<T, NDIM>(rho, g, pos, m);
     }
-}
-
-static int grid_blocks(long long N, int threads)
-{
-    long long b = (N + threads - 1) / threads;
-    const long long cap = (long long)num_sms() * 16;
-    if (b > cap) b = cap;
-    if (b < 1) b = 1;
-    return (int)b;
 }
 
 template <typename T>

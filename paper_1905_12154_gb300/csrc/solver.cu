@@ -22,43 +22,13 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "state.cuh"
 
 namespace bfm {
-
-struct SolverState {
-    double sigma;
-    double J_old;
-    double G;
-    double Gref;
-    double tol;
-    double beta1, beta2, alpha1, alpha2, sigma_min;
-    double mass_mu, mass_nu, max_mu, max_nu, min_mu, min_nu;
-    double last_resid;
-    int bad_mu, bad_nu;
-    int iter;
-    int max_iter;
-    int done;
-    int converged;
-    int nonfinite;
-    int pad;
-};
-
-struct Logs {
-    double* dual;
-    double* resid;
-    double* sigma;
-};
 
 // ---------------------------------------------------------------------------
 // small FP64 kernels
 // ---------------------------------------------------------------------------
-__device__ double block_sum_parts(const double* p, int n, double* red)
-{
-    double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
-    return block_sum(v, red);
-}
-
 template <typename T>
 __global__ void stats_kernel(const T* __restrict__ x, long long N, double* psum, double* pmax,
                              double* pmin, double* pbad)
@@ -129,19 +99,6 @@ __global__ void init_state_kernel(SolverState* st, double sigma0, double tol, in
     st->last_resid = 0.0;
 }
 
-__device__ double step_rule(const SolverState* st, double sigma, double gain, double G)
-{
-    if (gain < st->beta1 * sigma * G) {
-        const double s = st->alpha2 * sigma;
-        const double fl = fmin(st->sigma_min, sigma);
-        return fmax(s, fl);
-    }
-    if (gain > st->beta2 * sigma * G) return st->alpha1 * sigma;
-    return sigma;
-}
-
-// mode 0: J(phi_n) at the start of the phi-half (logged); 1: J(phi_{n+1/2});
-// mode 2: I(psi_{n+1/2}) at the start of the psi-half; 3: I(psi_{n+1}).
 __global__ void finalize_dual_kernel(SolverState* st, const double* pin, int nin,
                                      const double* pout, int nout, double hd, int mode, Logs logs)
 {
@@ -149,78 +106,41 @@ __global__ void finalize_dual_kernel(SolverState* st, const double* pin, int nin
     __shared__ double red[32];
     const double a = block_sum_parts(pin, nin, red);
     const double b = block_sum_parts(pout, nout, red);
-    if (threadIdx.x != 0) return;
-    const double J = hd * (a + b);
-    if (!isfinite(J)) { st->nonfinite = 1; st->done = 1; return; }
-    if (mode == 0) {
-        st->J_old = J;
-        if (logs.dual) logs.dual[st->iter] = J;
-        if (logs.sigma) logs.sigma[st->iter] = st->sigma;
-    } else if (mode == 2) {
-        st->J_old = J;
-    } else {
-        st->sigma = step_rule(st, st->sigma, J - st->J_old, st->G);
-        if (mode == 3) st->iter += 1;
-    }
+    if (threadIdx.x == 0) finalize_dual_body(st, hd * (a + b), mode, logs);
 }
 
-// mode 0: phi-half G -> residual, convergence; 1: psi-half G; 2: Gref.
 __global__ void finalize_G_kernel(SolverState* st, const double* part, int np, int mode, Logs logs)
 {
     if (mode != 2 && st->done) return;
     __shared__ double red[32];
     const double G = block_sum_parts(part, np, red);
-    if (threadIdx.x != 0) return;
-    if (!isfinite(G)) { st->nonfinite = 1; st->done = 1; return; }
-    if (mode == 2) { st->Gref = G; return; }
-    st->G = G;
-    if (mode == 0) {
-        const double r = st->Gref > 0.0 ? sqrt(fmax(G, 0.0) / st->Gref) : sqrt(fmax(G, 0.0));
-        st->last_resid = r;
-        if (logs.resid) logs.resid[st->iter] = r;
-        if (r < st->tol) { st->converged = 1; st->done = 1; }
-        else if (st->iter >= st->max_iter) st->done = 1;
-    }
+    if (threadIdx.x == 0) finalize_G_body(st, G, mode, logs);
 }
 
 // ---------------------------------------------------------------------------
 // workspace
 // ---------------------------------------------------------------------------
-static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-struct Workspace {
-    SolverState* state;
-    double* parts;            // kPartialSlots * kMaxPartials
-    double* logs;             // 3 * (max_iter + 1)
-    unsigned char* tables;    // per-axis tables
-    AxisTables tabs[3];
-    void* mu_n;
-    void* nu_n;
-    void* tmp;
-    void* rho;
-    size_t bytes;
-};
-
-static size_t tables_bytes(const Grid& g, int eb)
+size_t tables_bytes(const Grid& g, int eb)
 {
     size_t b = 0;
     for (int a = 0; a < g.ndim; ++a) b += axis_table_bytes(g.n[a], eb);
     return b;
 }
 
-static size_t poisson_bytes(const Grid& g, int eb)
+size_t poisson_bytes(const Grid& g, int eb)
 {
     return up256(sizeof(SolverState)) + up256(sizeof(double) * kPartialSlots * kMaxPartials) +
            tables_bytes(g, eb);
 }
 
-static size_t solve_bytes(const Grid& g, int eb, int max_iter)
+size_t solve_bytes(const Grid& g, int eb, int max_iter)
 {
     return poisson_bytes(g, eb) + up256(sizeof(double) * 3 * ((size_t)max_iter + 1)) +
            4 * up256((size_t)eb * g.N);
 }
 
-static void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Workspace* w, bool fields)
+void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Workspace* w, bool fields)
 {
     unsigned char* p = base;
     w->state = reinterpret_cast<SolverState*>(p); p += up256(sizeof(SolverState));
@@ -245,7 +165,7 @@ static void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Work
 }
 
 template <typename T>
-static bfm_status fill_tables(const Grid& g, Workspace* w, cudaStream_t st)
+bfm_status fill_tables(const Grid& g, Workspace* w, cudaStream_t st)
 {
     for (int a = 0; a < g.ndim; ++a) {
         // axes of equal length still get their own copy: simple and tiny
@@ -256,7 +176,7 @@ static bfm_status fill_tables(const Grid& g, Workspace* w, cudaStream_t st)
     return BFM_OK;
 }
 
-static bool fft_sizes_ok(const Grid& g)
+bool fft_sizes_ok(const Grid& g)
 {
     FftRadices rs;
     for (int a = 0; a < g.ndim; ++a)
@@ -264,7 +184,7 @@ static bool fft_sizes_ok(const Grid& g)
     return true;
 }
 
-static double* slot(Workspace* w, int s) { return w->parts + (size_t)s * kMaxPartials; }
+double* slot(Workspace* w, int s) { return w->parts + (size_t)s * kMaxPartials; }
 
 // ---------------------------------------------------------------------------
 // optional per-launch timing (bfm_profile_begin / bfm_profile_end)
@@ -361,7 +281,7 @@ static bfm_status poisson_inverse(const Grid& g, const AxisTables* tabs, T* buf,
 }
 
 template <typename T>
-static bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
+bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
                             Logs logs, cudaStream_t st)
 {
     const double hd = 1.0 / (double)g.N;
@@ -426,9 +346,9 @@ static bfm_status measure_density(const Grid& g, const T* x, Workspace* w, int w
     return BFM_OK;
 }
 
-static int elem_bytes(bfm_precision p) { return p == BFM_FP64 ? 8 : 4; }
+int elem_bytes(bfm_precision p) { return p == BFM_FP64 ? 8 : 4; }
 
-static Logs logs_of(Workspace* w, int max_iter)
+Logs logs_of(Workspace* w, int max_iter)
 {
     Logs logs;
     const int L = max_iter + 1;
@@ -446,7 +366,7 @@ __global__ void stop_now_kernel(SolverState* st)
 // Setup: validate and normalise the densities, fill the tables, measure
 // ||nu - 1||^2_{H^-1}, set phi_0 (= 0 unless warm-started) and the state.
 template <typename T>
-static bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int max_iter,
+bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int max_iter,
                             const bfm_options& o, unsigned char* wsp, cudaStream_t st, T* phi,
                             T* psi)
 {
@@ -516,7 +436,7 @@ static bfm_status read_done(const Grid& g, int eb, int max_iter, unsigned char* 
 // of a phi-half step) gives phi_n^c and J(phi_n); then psi = phi_n^c, the map
 // T = x - grad psi, W2^2 = 2 J(phi_n) and the logs.
 template <typename T>
-static bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, cudaStream_t st,
+bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, cudaStream_t st,
                               bfm_result* out)
 {
     Workspace w;
@@ -552,6 +472,13 @@ static bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, c
     out->converged = hs.converged;
     return hs.converged ? BFM_OK : BFM_NOT_CONVERGED;
 }
+
+template bfm_status init_impl<float>(const float*, const float*, const Grid&, double, int,
+                                     const bfm_options&, unsigned char*, cudaStream_t, float*, float*);
+template bfm_status init_impl<double>(const double*, const double*, const Grid&, double, int,
+                                      const bfm_options&, unsigned char*, cudaStream_t, double*, double*);
+template bfm_status finish_impl<float>(const Grid&, int, unsigned char*, cudaStream_t, bfm_result*);
+template bfm_status finish_impl<double>(const Grid&, int, unsigned char*, cudaStream_t, bfm_result*);
 
 }  // namespace bfm
 

@@ -1,0 +1,119 @@
+// state.cuh -- solver state, per-half-step scalar logic and workspace layout,
+// shared by the single-problem solver (solver.cu) and the batched solver
+// (batched.cu).
+#pragma once
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bfm {
+
+struct SolverState {
+    double sigma;
+    double J_old;
+    double G;
+    double Gref;
+    double tol;
+    double beta1, beta2, alpha1, alpha2, sigma_min;
+    double mass_mu, mass_nu, max_mu, max_nu, min_mu, min_nu;
+    double last_resid;
+    int bad_mu, bad_nu;
+    int iter;
+    int max_iter;
+    int done;
+    int converged;
+    int nonfinite;
+    int pad;
+};
+
+struct Logs {
+    double* dual;
+    double* resid;
+    double* sigma;
+};
+
+inline size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Workspace {
+    SolverState* state;
+    double* parts;            // kPartialSlots * kMaxPartials
+    double* logs;             // 3 * (max_iter + 1)
+    unsigned char* tables;    // per-axis tables
+    AxisTables tabs[3];
+    void* mu_n;
+    void* nu_n;
+    void* tmp;
+    void* rho;
+    size_t bytes;
+};
+
+size_t tables_bytes(const Grid& g, int eb);
+size_t poisson_bytes(const Grid& g, int eb);
+size_t solve_bytes(const Grid& g, int eb, int max_iter);
+void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Workspace* w, bool fields);
+bool fft_sizes_ok(const Grid& g);
+double* slot(Workspace* w, int s);
+Logs logs_of(Workspace* w, int max_iter);
+int elem_bytes(bfm_precision p);
+template <typename T> bfm_status fill_tables(const Grid& g, Workspace* w, cudaStream_t st);
+template <typename T>
+bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int max_iter,
+                     const bfm_options& o, unsigned char* wsp, cudaStream_t st, T* phi, T* psi);
+template <typename T>
+bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, cudaStream_t st,
+                       bfm_result* out);
+
+// ---------------------------------------------------------------------------
+// device-side scalar logic of one half step (run by one thread)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum_parts(const double* p, int n, double* red)
+{
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
+    return block_sum(v, red);
+}
+
+__device__ __forceinline__ double step_rule(const SolverState* st, double sigma, double gain, double G)
+{
+    if (gain < st->beta1 * sigma * G) {
+        const double s = st->alpha2 * sigma;
+        const double fl = fmin(st->sigma_min, sigma);
+        return fmax(s, fl);
+    }
+    if (gain > st->beta2 * sigma * G) return st->alpha1 * sigma;
+    return sigma;
+}
+
+// mode 0: J(phi_n) at the start of the phi-half (logged); 1: J(phi_{n+1/2});
+// mode 2: I(psi_{n+1/2}) at the start of the psi-half; 3: I(psi_{n+1}).
+__device__ __forceinline__ void finalize_dual_body(SolverState* st, double J, int mode, Logs logs)
+{
+    if (!isfinite(J)) { st->nonfinite = 1; st->done = 1; return; }
+    if (mode == 0) {
+        st->J_old = J;
+        if (logs.dual) logs.dual[st->iter] = J;
+        if (logs.sigma) logs.sigma[st->iter] = st->sigma;
+    } else if (mode == 2) {
+        st->J_old = J;
+    } else {
+        st->sigma = step_rule(st, st->sigma, J - st->J_old, st->G);
+        if (mode == 3) st->iter += 1;
+    }
+}
+
+// mode 0: phi-half G -> residual, convergence; 1: psi-half G; 2: Gref.
+__device__ __forceinline__ void finalize_G_body(SolverState* st, double G, int mode, Logs logs)
+{
+    if (!isfinite(G)) { st->nonfinite = 1; st->done = 1; return; }
+    if (mode == 2) { st->Gref = G; return; }
+    st->G = G;
+    if (mode == 0) {
+        const double r = st->Gref > 0.0 ? sqrt(fmax(G, 0.0) / st->Gref) : sqrt(fmax(G, 0.0));
+        st->last_resid = r;
+        if (logs.resid) logs.resid[st->iter] = r;
+        if (r < st->tol) { st->converged = 1; st->done = 1; }
+        else if (st->iter >= st->max_iter) st->done = 1;
+    }
+}
+
+}  // namespace bfm
