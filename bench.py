@@ -155,6 +155,61 @@ def workload_config(n):
             "l2": "inputs larger than L2 (6 resident fields of 64 MiB each)", "tol": 1e-3}
 
 
+def other_workloads(B, dev, stream, args) -> dict:
+    """The 384^3 3D solve, 128 batched uneven problems and the 32-pair loss."""
+    import numpy as np
+    import torch
+    import synthetic_inputs as si
+    out = {}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record(stream); r = fn(); b.record(stream)
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b) / 1e3
+
+    # 3D: ball -> 4 anisotropic Gaussians, 384^3, FP32
+    mu_h, nu_h = si.workload_ball_4g_384(384)
+    mu = torch.from_numpy(mu_h).to(dev, torch.float32)
+    nu = torch.from_numpy(nu_h).to(dev, torch.float32)
+    del mu_h, nu_h
+    s3 = B.BfmSolver(mu, nu, tol=0.0, max_iter=40)
+    s3.iterate(3)
+    _, t = timed(lambda: s3.iterate(20))
+    N3 = mu.numel()
+    r3, t3 = timed(lambda: B.bfm_solve(mu, nu, tol=args.tol, max_iter=1000, with_map=False))
+    out["ball_4g_384_fp32"] = {
+        "grid": [384, 384, 384], "iters_per_s": 20 / t, "ms_per_iter": t / 20 * 1e3,
+        "alg_hbm_frac_per_iter": (256 * N3 * 20 / t) / 1e9 / peaks()[0]["hbm_gbs"],
+        "time_to_tol_s": t3, "iters_to_tol": r3["iters"], "converged": r3["converged"],
+        "w2sq": r3["w2sq"], "max_density_ratio": max(r3["max_mu"], r3["max_nu"])}
+    del s3, mu, nu, r3
+    torch.cuda.empty_cache()
+    # batched: 128 problems, sides in {64,128,256,512}, FP32, per-problem tol 1e-4
+    probs = si.workload_batched_uneven()
+    mus = [torch.from_numpy(m).to(dev, torch.float32) for m, _ in probs]
+    nus = [torch.from_numpy(v).to(dev, torch.float32) for _, v in probs]
+    rb, tb = timed(lambda: B.bfm_solve_batched(mus, nus, tol=1e-4, max_iter=300))
+    iters = np.array([r["iters"] for r in rb])
+    out["batched_128_uneven_fp32"] = {
+        "problems": len(rb), "sides": sorted(set(int(m.shape[0]) for m in mus)),
+        "solves_per_s": len(rb) / tb, "seconds": tb, "tol": 1e-4, "max_iter": 300,
+        "converged": int(sum(r["converged"] for r in rb)),
+        "iters_median": float(np.median(iters)), "iters_max": int(iters.max()),
+        "cells": int(sum(m.numel() for m in mus))}
+    del mus, nus, rb
+    # loss: 32 pairs at 256^2, forward to 1e-5 (or 500 iterations) and backward
+    pairs = si.workload_loss_pairs_256()
+    mu = torch.stack([torch.from_numpy(p[0]) for p in pairs]).to(dev, torch.float32).requires_grad_(True)
+    nu = torch.stack([torch.from_numpy(p[1]) for p in pairs]).to(dev, torch.float32).requires_grad_(True)
+    loss, tf = timed(lambda: B.w2_loss(mu, nu, tol=1e-5, max_iter=500))
+    _, tbk = timed(lambda: torch.autograd.grad(loss.sum(), [mu, nu]))
+    out["loss_32x256_fp32"] = {"pairs": 32, "forward_s": tf, "backward_s": tbk,
+                               "pairs_per_s": 32 / (tf + tbk)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -166,6 +221,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-budget-s", type=float, default=150.0)
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the 3D, batched and loss workloads")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
@@ -299,6 +356,9 @@ def main():
                        "seconds_per_solve": te, "iters_per_solve": re["iters"],
                        "h2d_bytes_per_solve": h2d, "d2h_bytes_per_solve": d2h,
                        "call": "bfm_solve_host (pinned host mu, nu -> phi, psi, map), tol 1e-3"}
+        # ---- the other workloads: 3D, batched uneven solves, the W2^2 loss ---------------
+        if not args.no_workloads:
+            line["workloads"] = other_workloads(B, dev, stream, args)
         # ---- the FP64 CPU oracle on the host cores ----------------------------------------
         if ws == 1 and not args.no_cpu_baseline:
             import oracle
