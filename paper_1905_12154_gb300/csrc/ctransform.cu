@@ -41,7 +41,8 @@ struct CtArgs {
     LineTiles lt;
     int G;                // threads per line (power of two)
     int LD;               // shared leading dimension of f (elements)
-    int LDI;              // shared leading dimension of the index arrays
+    int LDI;              // shared leading dimension of the index stacks
+    int LDH;              // shared leading dimension of the compacted envelope
     T hh;                 // h^2 / 2 on this axis
     int negate;           // the pass reads -in
     int vec4;             // rows may be moved as float4 (n % 4 == 0, 16-byte aligned)
@@ -84,10 +85,11 @@ __device__ __forceinline__ bool hidden_v(int a, T fa, int b, T fb, int c, T fc, 
 }
 
 // Phase B: merge the envelopes of thread groups [t, t+s) and [t+s, t+2s).
-// beg/end hold chunk-space positions into the stack.  The left chain's last
-// two parabolas (a, b) and the right chain's first two (c, d) are kept in
-// registers with their stack positions, so each pop costs one stack read and
-// one value read; emptied segments are written back as they are passed.
+// beg/end hold chunk-space positions into the stacks; the parabola at stack
+// position p has its index in stk and its value in f at that position (the
+// stacks are built in place over the line values).  The left chain's last
+// two parabolas (a, b) and the right chain's first two (c, d) stay in
+// registers, so a pop costs one pair of independent loads.
 template <int K, typename T>
 __device__ void merge_pair(const T* f, const short* stk, short* beg, short* end,
                            int t, int s, int n, T hh)
@@ -116,11 +118,11 @@ __device__ void merge_pair(const T* f, const short* stk, short* beg, short* end,
         if (rd < tr) { pd = beg[rd]; endrd = end[rd]; } else pd = -1;
     }
     int ib = stk[SK::s(pb)], ic = stk[SK::s(pc)];
-    int ia = pa >= 0 ? (int)stk[SK::s(pa)] : -1;
-    int id = pd >= 0 ? (int)stk[SK::s(pd)] : -1;
-    T fb = f[SK::f(ib)], fc = f[SK::f(ic)];
-    T fa = ia >= 0 ? f[SK::f(ia)] : (T)0;
-    T fd = id >= 0 ? f[SK::f(id)] : (T)0;
+    T fb = f[SK::f(pb)], fc = f[SK::f(pc)];
+    int ia = -1, id = -1;
+    T fa = (T)0, fd = (T)0;
+    if (pa >= 0) { ia = stk[SK::s(pa)]; fa = f[SK::f(pa)]; }
+    if (pd >= 0) { id = stk[SK::s(pd)]; fd = f[SK::f(pd)]; }
     for (int guard = 0; guard <= n + 2; ++guard) {
         if (ia >= 0 && hidden_v(ia, fa, ib, fb, ic, fc, hh)) {
             // pop b; if it was the last parabola of thread lt, that segment empties
@@ -132,8 +134,7 @@ __device__ void merge_pair(const T* f, const short* stk, short* beg, short* end,
                 while (la >= tl && beg[la] == end[la]) --la;
                 if (la >= tl) { pa = end[la] - 1; begla = beg[la]; } else pa = -1;
             }
-            ia = pa >= 0 ? (int)stk[SK::s(pa)] : -1;
-            fa = ia >= 0 ? f[SK::f(ia)] : (T)0;
+            if (pa >= 0) { ia = stk[SK::s(pa)]; fa = f[SK::f(pa)]; } else ia = -1;
             continue;
         }
         if (id >= 0 && hidden_v(ib, fb, ic, fc, id, fd, hh)) {
@@ -146,14 +147,22 @@ __device__ void merge_pair(const T* f, const short* stk, short* beg, short* end,
                 while (rd < tr && beg[rd] == end[rd]) ++rd;
                 if (rd < tr) { pd = beg[rd]; endrd = end[rd]; } else pd = -1;
             }
-            id = pd >= 0 ? (int)stk[SK::s(pd)] : -1;
-            fd = id >= 0 ? f[SK::f(id)] : (T)0;
+            if (pd >= 0) { id = stk[SK::s(pd)]; fd = f[SK::f(pd)]; } else id = -1;
             continue;
         }
         break;
     }
     end[lt] = (short)(pb + 1);
     beg[rt] = (short)pc;
+}
+
+// Barrier over the G threads of one line: a line of 32 or fewer threads lies
+// in one warp; larger lines (whole warps, at most 8 per CTA) use named
+// barrier 1 + w so the lines of a CTA do not wait for one another.
+__device__ __forceinline__ void line_sync(int w, int G)
+{
+    if (G <= 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" :: "r"(1 + w), "r"(G) : "memory");
 }
 
 // BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
@@ -170,9 +179,10 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
     const int G = a.G;
     const int W = lt.W;
     T* fs = reinterpret_cast<T*>(smem_raw);
-    short* stk_all = reinterpret_cast<short*>(fs + (size_t)W * a.LD);
-    short* hull_all = stk_all + (size_t)W * a.LDI;
-    short* beg_all = hull_all + (size_t)W * a.LDI;
+    T* hval_all = fs + (size_t)W * a.LD;
+    short* stk_all = reinterpret_cast<short*>(hval_all + (size_t)W * a.LDH);
+    short* hidx_all = stk_all + (size_t)W * a.LDI;
+    short* beg_all = hidx_all + (size_t)W * a.LDH;
     short* end_all = beg_all + (size_t)W * G;
     int* wsum_all = reinterpret_cast<int*>(end_all + (size_t)W * G);   // 4-byte aligned
     const int nwl = (G + 31) / 32;                 // warps per line
@@ -183,8 +193,9 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
     const int w = tid / G, t = tid - w * G;
     const int lane = tid & 31;
     T* f = fs + (size_t)w * a.LD;
+    T* hval = hval_all + (size_t)w * a.LDH;
     short* stk = stk_all + (size_t)w * a.LDI;
-    short* hull = hull_all + (size_t)w * a.LDI;
+    short* hidx = hidx_all + (size_t)w * a.LDH;
     short* beg = beg_all + w * G;
     short* end = end_all + w * G;
     const T hh = a.hh;
@@ -238,22 +249,28 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
         __syncthreads();
         const bool active = (w < tl.wact);
         // ---- A: envelope of this thread's chunk ------------------------------
+        // The stack lives in place: position p of the chunk holds the index
+        // (stk) and value (f) of the p-th stacked parabola; a push writes at
+        // the new top, which is never beyond the cell being read.
         if (active) {
             if (lo < n) {
-                // the top two stack entries live in registers
-                int top = lo;                          // chunk-space position of the top
-                int s1 = lo, s0 = -1;                  // top, second
+                int top = lo;
+                int s1 = lo, s0 = -1;
+                T v1 = f[SK::f(lo)], v0 = (T)0;
                 stk[SK::s(lo)] = (short)lo;
                 for (int q = lo + 1; q < hi; ++q) {
-                    while (s0 >= 0 && hidden<K>(f, s0, s1, q, hh)) {
+                    const T vq = f[SK::f(q)];
+                    while (s0 >= 0 && hidden_v(s0, v0, s1, v1, q, vq, hh)) {
                         --top;
-                        s1 = s0;
-                        s0 = (top > lo) ? (int)stk[SK::s(top - 1)] : -1;
+                        s1 = s0; v1 = v0;
+                        if (top > lo) { s0 = stk[SK::s(top - 1)]; v0 = f[SK::f(top - 1)]; }
+                        else s0 = -1;
                     }
                     ++top;
                     stk[SK::s(top)] = (short)q;
-                    s0 = s1;
-                    s1 = q;
+                    f[SK::f(top)] = vq;
+                    s0 = s1; v0 = v1;
+                    s1 = q; v1 = vq;
                 }
                 beg[t] = (short)lo;
                 end[t] = (short)(top + 1);
@@ -262,17 +279,17 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
                 end[t] = 0;
             }
         }
-        __syncthreads();
+        line_sync(w, G);
         // ---- B: pairwise merges ------------------------------------------------
         for (int s = 1; s < G; s <<= 1) {
             if (active && (t & (2 * s - 1)) == 0 && t + s < G) merge_pair<K>(f, stk, beg, end, t, s, n, hh);
-            // the next level merges groups of 4s threads: inside one warp, a warp
-            // barrier publishes this level's segment updates; otherwise a CTA barrier
+            // the next level merges groups of 4s threads: inside one warp a warp
+            // barrier publishes this level's segment updates, else the line barrier
             if (4 * s <= 32) __syncwarp();
-            else __syncthreads();
+            else line_sync(w, G);
         }
-        __syncthreads();
-        // ---- C: compaction -------------------------------------------------------
+        line_sync(w, G);
+        // ---- C: compaction of (index, value) pairs ---------------------------------
         const int cnt = active ? (end[t] - beg[t]) : 0;
         int incl = cnt;
         const int width = G < 32 ? G : 32;
@@ -282,7 +299,7 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
         }
         if (G > 32) {
             if (active && (t & 31) == 31) wsum_all[w * nwl + (t >> 5)] = incl;
-            __syncthreads();
+            line_sync(w, G);
             int add = 0;
             if (active)
                 for (int i = 0; i < (t >> 5); ++i) add += wsum_all[w * nwl + i];
@@ -292,44 +309,40 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
         if (active) {
             const int b0 = beg[t];
             const int excl = incl - cnt;
-            for (int i = 0; i < cnt; ++i) hull[excl + i] = stk[SK::s(b0 + i)];
+            for (int i = 0; i < cnt; ++i) {
+                hidx[excl + i] = stk[SK::s(b0 + i)];
+                hval[excl + i] = f[SK::f(b0 + i)];
+            }
         }
-        __syncthreads();
-        // ---- D: evaluate this thread's outputs -----------------------------------
-        T outv[K];
+        line_sync(w, G);
+        // ---- D: evaluate this thread's outputs into the (now free) value array -----
         if (active && lo < n) {
             const int H = htot[w];
             int kl = 0, kh = H - 1;
             while (kl < kh) {
                 const int mid = (kl + kh) >> 1;
-                const int j0 = hull[mid], j1 = hull[mid + 1];
-                if (parab(hh, lo, j1, f[SK::f(j1)]) < parab(hh, lo, j0, f[SK::f(j0)])) kl = mid + 1;
+                const int j0 = hidx[mid], j1 = hidx[mid + 1];
+                const T g0 = hval[mid], g1 = hval[mid + 1];
+                if (parab(hh, lo, j1, g1) < parab(hh, lo, j0, g0)) kl = mid + 1;
                 else kh = mid;
             }
             int k = kl;
-            int jc = hull[k];
-            T fc = f[SK::f(jc)];
-#pragma unroll
-            for (int q = 0; q < K; ++q) {
-                const int x = lo + q;
-                if (x < hi) {
-                    T vc = parab(hh, x, jc, fc);
-                    while (k + 1 < H) {
-                        const int jn = hull[k + 1];
-                        const T fn = f[SK::f(jn)];
-                        const T vn = parab(hh, x, jn, fn);
-                        if (vn <= vc) { ++k; jc = jn; fc = fn; vc = vn; }
-                        else break;
-                    }
-                    outv[q] = vc;
+            int jc = hidx[k];
+            T fc = hval[k];
+            int jn = -1;
+            T fn = (T)0;
+            if (k + 1 < H) { jn = hidx[k + 1]; fn = hval[k + 1]; }
+            for (int x = lo; x < hi; ++x) {
+                T vc = parab(hh, x, jc, fc);
+                while (jn >= 0) {
+                    const T vn = parab(hh, x, jn, fn);
+                    if (vn <= vc) {
+                        ++k; jc = jn; fc = fn; vc = vn;
+                        if (k + 1 < H) { jn = hidx[k + 1]; fn = hval[k + 1]; } else jn = -1;
+                    } else break;
                 }
+                f[SK::f(x)] = vc;
             }
-        }
-        __syncthreads();
-        if (active && lo < n) {
-#pragma unroll
-            for (int q = 0; q < K; ++q)
-                if (lo + q < hi) f[SK::f(lo + q)] = outv[q];
         }
         __syncthreads();
         // ---- store ---------------------------------------------------------------
@@ -450,15 +463,19 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
     p.G = next_pow2((n + p.K - 1) / p.K);
     const bool contig = (axis == 0);
     const int chunks = (n + p.K - 1) / p.K + 1;
-    const int LDI = n + 2 * chunks + (n & 1) + 8;        // skewed index stack (two shorts per chunk)
+    int LDI = n + 2 * chunks + 8;                         // skewed index stack (two shorts per chunk)
+    LDI += LDI & 1;
     const int nf = n + chunks + 1;                        // skewed values (one word per chunk)
-    // lines per CTA: at most 1024 threads, at most 32 lines, a shared-memory budget
-    const size_t line_bytes = (size_t)(nf + 32) * elem_bytes + 2 * (size_t)LDI * 2 + 2 * (size_t)p.G * 2 + 64;
-    // up to 512 threads per CTA so that two CTAs share an SM
+    const int LDH = n + (n & 1);                          // compacted envelope
+    const int nwl = (p.G + 31) / 32;
+    const size_t line_bytes = (size_t)(nf + 32) * elem_bytes + (size_t)LDH * elem_bytes +
+                              (size_t)LDI * 2 + (size_t)LDH * 2 + 4 * (size_t)p.G + 4 * nwl + 64;
+    // up to 512 threads per CTA so that two CTAs share an SM; lines of more
+    // than one warp use named barriers 1..8, so at most 8 such lines
     int W = 512 / p.G;
     if (W < 1) W = 1;
     if (W > 32) W = 32;
-    const size_t budget = 110 * 1024;                      // two CTAs per SM
+    const size_t budget = 110 * 1024;
     while (W > 1 && (size_t)W * line_bytes > budget) --W;
     if (!contig) {
         // interleaved tiles: W a power of two (division-free index math)
@@ -476,12 +493,13 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
             if (c < best) { best = c; LD = cand; }
         }
     }
+    LD += LD & 1;
     p.W = W;
     p.LD = LD;
     p.LDI = LDI;
-    const int nwl = (p.G + 31) / 32;
-    p.smem = (size_t)W * LD * elem_bytes + 2 * (size_t)W * LDI * 2 + 2 * (size_t)W * p.G * 2 +
-             (size_t)W * nwl * 4 + (size_t)W * 4 + 16;
+    p.LDH = LDH;
+    p.smem = (size_t)W * LD * elem_bytes + (size_t)W * LDH * elem_bytes + (size_t)W * LDI * 2 +
+             (size_t)W * LDH * 2 + 2 * (size_t)W * p.G * 2 + (size_t)W * nwl * 4 + (size_t)W * 4 + 16;
     p.threads = ((W * p.G + 31) / 32) * 32;
     p.tiles = make_tiles(g, axis, W);
     return p;
@@ -495,7 +513,7 @@ static CtArgs<T> make_ct_args(const Grid& g, int axis, const CtPlan& p, const T*
     CtArgs<T> a;
     a.in = in; a.out = out; a.w_in = w_in; a.w_out = w_out;
     a.part_in = part_in; a.part_out = part_out; a.done = done;
-    a.lt = p.tiles; a.G = p.G; a.LD = p.LD; a.LDI = p.LDI;
+    a.lt = p.tiles; a.G = p.G; a.LD = p.LD; a.LDI = p.LDI; a.LDH = p.LDH;
     const double h = 1.0 / g.n[axis];
     a.hh = (T)(0.5 * h * h);
     a.negate = negate ? 1 : 0;

@@ -52,6 +52,8 @@ struct DctArgs {
     unsigned mag[kMaxStages]; // ceil(2^32 / Ls[s]): b / Ls[s] = umulhi(b, mag[s]) for b < n
     int lnp;                  // log2(pairs per tile) for interleaved tiles
     double gscale;            // MID: 1 / N^2
+    int fnst;                 // register Stockham path: number of passes
+    int frad[8];              // and their radices (16, ..., 16, last in {2,4,8,16})
 };
 
 __device__ __forceinline__ int div_by(int b, int L, unsigned mag)
@@ -317,6 +319,348 @@ dct_pass_kernel(DctArgs<T> a0, const DctArgs<T>* batch)
 }
 
 // ---------------------------------------------------------------------------
+// FP32 lines of power-of-two length: register Stockham FFT
+// ---------------------------------------------------------------------------
+// Each of the T = n/16 threads of a line pair holds 16 complex values per
+// pass and applies radix-R butterflies (R = 16, the last pass 2, 4, 8 or 16)
+// in registers.  A Stockham pass reads element j + r n/R, twiddles by
+// e^{-+2 pi i (j mod Ns) r / (Ns R)}, transforms over r and writes
+// ((j - j mod Ns) R + j mod Ns) + r Ns, so input and output are both in
+// natural order and no digit reversal is needed.  Shared memory holds the
+// pair with one pad element per 16, which keeps every pass's reads and writes
+// free of bank conflicts.  Reads complete (barrier) before writes: in place.
+__device__ __forceinline__ int padix(int i) { return i + (i >> 4); }
+
+template <int SIGN>
+__device__ __forceinline__ float2 cmul_sgn(float2 a, float2 w)
+{
+    // a * w (SIGN < 0) or a * conj(w) (SIGN > 0)
+    float2 r;
+    if (SIGN < 0) { r.x = a.x * w.x - a.y * w.y; r.y = a.x * w.y + a.y * w.x; }
+    else          { r.x = a.x * w.x + a.y * w.y; r.y = a.y * w.x - a.x * w.y; }
+    return r;
+}
+
+// radix-4 in place on v[o], v[o+s], v[o+2s], v[o+3s]
+template <int SIGN, typename A>
+__device__ __forceinline__ void r4(A& v, int o, int s)
+{
+    const float2 a0 = cadd(v[o], v[o + 2 * s]), a1 = csub(v[o], v[o + 2 * s]);
+    const float2 b0 = cadd(v[o + s], v[o + 3 * s]), b1 = csub(v[o + s], v[o + 3 * s]);
+    float2 ib1;
+    if (SIGN < 0) { ib1.x = b1.y; ib1.y = -b1.x; } else { ib1.x = -b1.y; ib1.y = b1.x; }
+    v[o] = cadd(a0, b0);
+    v[o + 2 * s] = csub(a0, b0);
+    v[o + s] = cadd(a1, ib1);
+    v[o + 3 * s] = csub(a1, ib1);
+}
+
+// X[k] = sum_m v[O+m] e^{SIGN 2 pi i m k / R}, in place on v[O..O+R); X[k] is
+// left in slot O + out_slot<R>(k) (radix 8 and 16 leave their outputs transposed)
+template <int R>
+__host__ __device__ constexpr int out_slot(int k)
+{
+    return R == 16 ? 4 * (k % 4) + k / 4 : R == 8 ? 2 * (k % 4) + k / 4 : k;
+}
+
+template <int R, int SIGN, int O>
+__device__ __forceinline__ void dft_reg(float2 (&v)[16])
+{
+    if (R == 2) {
+        const float2 a = v[O], b = v[O + 1];
+        v[O] = cadd(a, b); v[O + 1] = csub(a, b);
+    } else if (R == 4) {
+        r4<SIGN>(v, O, 1);
+    } else if (R == 8) {
+        // m = 2 m1 + m2: radix-4 over m1, twiddle W8^(m2 k1), radix-2 over m2
+        r4<SIGN>(v, O, 2);
+        r4<SIGN>(v, O + 1, 2);
+        const float c = 0.70710678118654752440f;
+        float2 t;
+        t = v[O + 3]; v[O + 3].x = c * (t.x - SIGN * t.y); v[O + 3].y = c * (t.y + SIGN * t.x);
+        t = v[O + 5]; v[O + 5].x = -SIGN * t.y;           v[O + 5].y = SIGN * t.x;   // times SIGN i
+        t = v[O + 7]; v[O + 7].x = c * (-t.x - SIGN * t.y); v[O + 7].y = c * (-t.y + SIGN * t.x);
+        // X[k1 + 4 k2] is left at v[O + 2 k1 + k2] (see out_slot)
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            const float2 a = v[O + 2 * k1], b = v[O + 2 * k1 + 1];
+            v[O + 2 * k1] = cadd(a, b);
+            v[O + 2 * k1 + 1] = csub(a, b);
+        }
+    } else {  // R == 16: m = 4 m1 + m2: radix-4 over m1, twiddle W16^(m2 k1), radix-4 over m2
+#pragma unroll
+        for (int m2 = 0; m2 < 4; ++m2) r4<SIGN>(v, O + m2, 4);        // v[O + m2 + 4 k1]
+        const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
+        const float c2 = 0.70710678118654752440f;
+#pragma unroll
+        for (int m2 = 1; m2 < 4; ++m2)
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) {
+                const int m = m2 * k1;                       // W16^m, m in {1,2,3,4,6,9}
+                const float wc = (m == 1) ? c1 : (m == 2) ? c2 : (m == 3) ? s1 : (m == 4) ? 0.f
+                               : (m == 6) ? -c2 : -c1;
+                const float ws = (m == 1) ? s1 : (m == 2) ? c2 : (m == 3) ? c1 : (m == 4) ? 1.f
+                               : (m == 6) ? c2 : -s1;
+                // W16^m = cos(2 pi m/16) + SIGN i sin(2 pi m/16)
+                const float2 a = v[O + m2 + 4 * k1];
+                float2 b;
+                b.x = a.x * wc - SIGN * a.y * ws;
+                b.y = a.y * wc + SIGN * a.x * ws;
+                v[O + m2 + 4 * k1] = b;
+            }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) r4<SIGN>(v, O + 4 * k1, 1);   // X[k1 + 4 k2] left at v[O + 4 k1 + k2]
+    }
+}
+
+template <int R, int SIGN, int Bi>
+__device__ __forceinline__ void read_bfly(const float2* z, int n, int Ns, int t, int T,
+                                          const float2* tw, float2 (&v)[16])
+{
+    const int step = n / (Ns * R);
+    const int j = t + Bi * T;
+    const int k = j & (Ns - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[Bi * R + r] = z[padix(j + r * (n / R))];
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[Bi * R + r] = cmul_sgn<SIGN>(v[Bi * R + r], tw[(k * r) * step]);
+    dft_reg<R, SIGN, Bi * R>(v);
+}
+
+template <int R, int SIGN>
+__device__ __forceinline__ void pass_read(const float2* z, int n, int Ns, int t, int T,
+                                          const float2* tw, float2 (&v)[16])
+{
+    read_bfly<R, SIGN, 0>(z, n, Ns, t, T, tw, v);
+    if (16 / R > 1) read_bfly<R, SIGN, (16 / R > 1 ? 1 : 0)>(z, n, Ns, t, T, tw, v);
+    if (16 / R > 2) {
+        read_bfly<R, SIGN, (16 / R > 2 ? 2 : 0)>(z, n, Ns, t, T, tw, v);
+        read_bfly<R, SIGN, (16 / R > 2 ? 3 : 0)>(z, n, Ns, t, T, tw, v);
+    }
+    if (16 / R > 4) {
+#pragma unroll
+        for (int b = 4; b < 8; ++b) {
+            const int step = n / (Ns * R);
+            const int j = t + b * T;
+            const int k = j & (Ns - 1);
+            float2 x0 = z[padix(j)], x1 = z[padix(j + n / R)];
+            x1 = cmul_sgn<SIGN>(x1, tw[k * step]);
+            v[2 * b] = cadd(x0, x1);
+            v[2 * b + 1] = csub(x0, x1);
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void pass_write(float2* z, int Ns, int t, int T, const float2 (&v)[16])
+{
+    constexpr int B = 16 / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = t + b * T;
+        const int k = j & (Ns - 1);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) z[padix(base + r * Ns)] = v[b * R + out_slot<R>(r)];
+    }
+}
+
+// One FFT of every pair held by the CTA (all threads take part: barriers).
+template <int SIGN>
+__device__ void stockham_fft(float2* z, int n, int t, int T, bool active, const float2* tw,
+                             int nst, const int* rad)
+{
+    float2 v[16];
+    int Ns = 1;
+    for (int s = 0; s < nst; ++s) {
+        const int R = rad[s];
+        if (active) {
+            if (R == 16) pass_read<16, SIGN>(z, n, Ns, t, T, tw, v);
+            else if (R == 8) pass_read<8, SIGN>(z, n, Ns, t, T, tw, v);
+            else if (R == 4) pass_read<4, SIGN>(z, n, Ns, t, T, tw, v);
+            else pass_read<2, SIGN>(z, n, Ns, t, T, tw, v);
+        }
+        __syncthreads();
+        if (active) {
+            if (R == 16) pass_write<16>(z, Ns, t, T, v);
+            else if (R == 8) pass_write<8>(z, Ns, t, T, v);
+            else if (R == 4) pass_write<4>(z, Ns, t, T, v);
+            else pass_write<2>(z, Ns, t, T, v);
+        }
+        __syncthreads();
+        Ns *= R;
+    }
+}
+
+template <int MODE, bool CONTIG, bool BATCHED>
+__global__ void __launch_bounds__(512, 1) dct_fast_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
+{
+    using C = float2;
+    using T = float;
+    const DctArgs<float>& a = BATCHED ? batch[blockIdx.y] : a0;
+    if (BATCHED && blockIdx.x >= a.lt.ntiles) return;
+    if (a.done && *a.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* zs = reinterpret_cast<C*>(smem_raw);
+    __shared__ double red[32];
+    const LineTiles& lt = a.lt;
+    const int n = lt.n;
+    const int G = a.G;                      // threads per pair = n / 16
+    const int tid = threadIdx.x;
+    const int pp = tid / G, t = tid - pp * G;
+    C* z = zs + (size_t)pp * a.LDZ;
+    const T inv_n = (T)1 / (T)n;
+    T sig = (T)0;
+    if (MODE == DCT_INV && a.upd) sig = (T)(*a.sigma);
+    double acc = 0.0;
+    Acc<T> gsum;
+
+    for (long long tile = blockIdx.x; tile < lt.ntiles; tile += gridDim.x) {
+        const Tile tl = tile_at(lt, tile);
+        const int np = (tl.wact + 1) / 2;
+        const bool active = (pp < np);
+        // ---- load: natural order of the reordered sequence (FWD/MID) or spectrum (INV)
+        {
+            const int np_pow = CONTIG ? 1 : (1 << a.lnp);
+            const int per = CONTIG ? n : np_pow * n;
+            const int reps = CONTIG ? np : 1;
+            for (int q0 = 0; q0 < reps; ++q0)
+            for (int e = tid; e < per; e += blockDim.x) {
+                int q, j;
+                if (CONTIG) { q = q0; j = e; }
+                else        { q = e & (np_pow - 1); j = e >> a.lnp; }
+                if (q >= np) continue;
+                const int lb = 2 * q + 1;
+                const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                T xa = a.in[ada];
+                T xb = (T)0;
+                if (lb < tl.wact) xb = a.in[ada + tl.lstride];
+                if (MODE == DCT_FWD && a.base) {
+                    xa = a.base[ada] - xa;
+                    if (lb < tl.wact) xb = a.base[ada + tl.lstride] - xb;
+                }
+                C v; v.x = xa; v.y = xb;
+                const int m = (MODE == DCT_INV) ? j : ((j & 1) ? (n - 1 - (j >> 1)) : (j >> 1));
+                zs[(size_t)q * a.LDZ + padix(m)] = v;
+            }
+        }
+        __syncthreads();
+        if (MODE != DCT_INV) {
+            stockham_fft<-1>(z, n, t, G, active, a.tw, a.fnst, a.frad);
+            if (active) {
+                for (int k = t; k <= n / 2; k += G) {
+                    const int km = (n - k) % n;
+                    const C Zk = z[padix(k)], Zm = z[padix(km)];
+                    C A, Bq;
+                    A.x = (T)0.5 * (Zk.x + Zm.x); A.y = (T)0.5 * (Zk.y - Zm.y);
+                    Bq.x = (T)0.5 * (Zk.y + Zm.y); Bq.y = (T)0.5 * (Zm.x - Zk.x);
+                    const C dk = a.dtw[k];
+                    C outk; outk.x = dk.x * A.x - dk.y * A.y; outk.y = dk.x * Bq.x - dk.y * Bq.y;
+                    if (km != k) {
+                        C Am, Bm;
+                        Am.x = (T)0.5 * (Zm.x + Zk.x); Am.y = (T)0.5 * (Zm.y - Zk.y);
+                        Bm.x = (T)0.5 * (Zm.y + Zk.y); Bm.y = (T)0.5 * (Zk.x - Zm.x);
+                        const C dm = a.dtw[km];
+                        C outm; outm.x = dm.x * Am.x - dm.y * Am.y; outm.y = dm.x * Bm.x - dm.y * Bm.y;
+                        z[padix(km)] = outm;
+                    }
+                    z[padix(k)] = outk;
+                }
+            }
+            __syncthreads();
+        }
+        if (MODE == DCT_MID) {
+            if (active) {
+                const int ia = tl.i0 + 2 * pp, ib = ia + 1;
+                const bool has_b = (2 * pp + 1 < tl.wact);
+                T La = a.lam_a0[ia], Lb = has_b ? a.lam_a0[ib] : (T)0;
+                T wa = (ia == 0) ? (T)1 : (T)2, wb = (ib == 0) ? (T)1 : (T)2;
+                if (a.lam_a1) {
+                    const int jo = (int)tl.outer;
+                    La += a.lam_a1[jo]; Lb += a.lam_a1[jo];
+                    const T wo = (jo == 0) ? (T)1 : (T)2;
+                    wa *= wo; wb *= wo;
+                }
+                for (int k = t; k < n; k += G) {
+                    const T lk = a.lam_axis[k];
+                    const T wk = (k == 0) ? (T)1 : (T)2;
+                    C v = z[padix(k)];
+                    const T la = La + lk, lb = Lb + lk;
+                    T ga = (T)0, gb = (T)0;
+                    if (la > (T)0) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
+                    if (has_b && lb > (T)0) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
+                    v.x = ga; v.y = gb;
+                    z[padix(k)] = v;
+                }
+            }
+            acc += gsum.take();
+            __syncthreads();
+        }
+        if (MODE != DCT_FWD) {
+            if (active) {
+                for (int k = t; k <= n / 2; k += G) {
+                    const int km = (n - k) % n;
+                    const C Xk = z[padix(k)], Xm = z[padix(km)];
+                    const T xam = (k == 0) ? (T)0 : Xm.x, xbm = (k == 0) ? (T)0 : Xm.y;
+                    const C dk = cconj(a.dtw[k]);
+                    C Va, Vb;
+                    Va.x = dk.x * Xk.x + dk.y * xam; Va.y = dk.y * Xk.x - dk.x * xam;
+                    Vb.x = dk.x * Xk.y + dk.y * xbm; Vb.y = dk.y * Xk.y - dk.x * xbm;
+                    C Zk; Zk.x = Va.x - Vb.y; Zk.y = Va.y + Vb.x;
+                    if (km != k) {
+                        const C dm = cconj(a.dtw[km]);
+                        C Wa, Wb;
+                        Wa.x = dm.x * Xm.x + dm.y * Xk.x; Wa.y = dm.y * Xm.x - dm.x * Xk.x;
+                        Wb.x = dm.x * Xm.y + dm.y * Xk.y; Wb.y = dm.y * Xm.y - dm.x * Xk.y;
+                        C Zm; Zm.x = Wa.x - Wb.y; Zm.y = Wa.y + Wb.x;
+                        z[padix(km)] = Zm;
+                    }
+                    z[padix(k)] = Zk;
+                }
+            }
+            __syncthreads();
+            stockham_fft<+1>(z, n, t, G, active, a.tw, a.fnst, a.frad);
+        }
+        // ---- store ------------------------------------------------------------------
+        {
+            const int np_pow = CONTIG ? 1 : (1 << a.lnp);
+            const int per = CONTIG ? n : np_pow * n;
+            const int reps = CONTIG ? np : 1;
+            for (int q0 = 0; q0 < reps; ++q0)
+            for (int e = tid; e < per; e += blockDim.x) {
+                int q, j;
+                if (CONTIG) { q = q0; j = e; }
+                else        { q = e & (np_pow - 1); j = e >> a.lnp; }
+                if (q >= np) continue;
+                const int lb = 2 * q + 1;
+                const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                C v;
+                if (MODE == DCT_FWD) {
+                    v = zs[(size_t)q * a.LDZ + padix(j)];
+                } else {
+                    const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
+                    v = zs[(size_t)q * a.LDZ + padix(m)];
+                    v.x *= inv_n;
+                    v.y *= inv_n;
+                }
+                if (MODE == DCT_INV && a.upd) {
+                    a.out[ada] = a.upd[ada] + sig * v.x;
+                    if (lb < tl.wact) a.out[ada + tl.lstride] = a.upd[ada + tl.lstride] + sig * v.y;
+                } else {
+                    a.out[ada] = v.x;
+                    if (lb < tl.wact) a.out[ada + tl.lstride] = v.y;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (MODE == DCT_MID && a.part) {
+        const double sacc = block_sum(acc, red);
+        if (threadIdx.x == 0) a.part[blockIdx.x] = sacc * a.gscale;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // tables: twiddles, digit reversal and eigenvalues (computed on the device in FP64)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -398,20 +742,41 @@ template bfm_status fill_axis_tables<double>(int, AxisTables*, unsigned char*, c
 // ---------------------------------------------------------------------------
 // launch planning
 // ---------------------------------------------------------------------------
+static bool fast_radices(int n, int* nst, int* rad)
+{
+    if (n < 32 || (n & (n - 1))) return false;
+    int k = 0;
+    while ((1 << k) < n) ++k;
+    int c = 0;
+    for (int i = 0; i < k / 4; ++i) rad[c++] = 16;
+    if (k % 4) rad[c++] = 1 << (k % 4);
+    *nst = c;
+    return c <= 8;
+}
+
 DctPlan plan_dct_pass(const Grid& g, int axis, int elem_bytes)
 {
     DctPlan p;
     const int n = g.n[axis];
     const bool contig = (axis == 0);
-    int G = n / 8;
-    if (G < 8) G = 8;
-    if (G > 256) G = 256;
-    G = (G + 7) & ~7;
+    int fr[8], fn = 0;
+    p.fast = (elem_bytes == 4 && fast_radices(n, &fn, fr)) ? 1 : 0;
+    int G, max_threads;
+    if (p.fast) {
+        G = n / 16;                                   // 16 complex values per thread per pass
+        max_threads = 512;                            // up to 128 registers per thread
+        p.LDZ = n + n / 16 + 1;                       // one pad element per 16
+    } else {
+        G = n / 8;
+        if (G < 8) G = 8;
+        if (G > 256) G = 256;
+        G = (G + 7) & ~7;
+        max_threads = elem_bytes == 8 ? 512 : 1024;   // FP64 gets 128 registers
+        p.LDZ = n + 1;
+    }
     p.G = G;
-    p.LDZ = n + 1;
     const size_t pair_bytes = (size_t)p.LDZ * 2 * elem_bytes;
     const size_t budget = 200 * 1024;
-    const int max_threads = elem_bytes == 8 ? 512 : 1024;   // FP64 gets 128 registers
     int W = 2 * (max_threads / G);
     while (W > 2 && (size_t)(W / 2) * pair_bytes > budget) W -= 2;
     if (W > 32) W = 32;
@@ -473,11 +838,27 @@ static bfm_status make_dct_args(const Grid& g, int axis, const DctPlan& p, const
     a->lnp = 0;
     while ((1 << a->lnp) < npt) ++a->lnp;
     a->gscale = 1.0 / ((double)g.N * (double)g.N);
+    a->fnst = 0;
+    for (int i = 0; i < 8; ++i) a->frad[i] = 0;
+    if (p.fast) fast_radices(g.n[axis], &a->fnst, a->frad);
     return BFM_OK;
 }
 
-static void* select_dct(int mode, int elem_bytes, bool contig, bool batched)
+template <int MODE>
+static void* dct_fast(bool contig, bool batched)
 {
+    if (batched)
+        return contig ? (void*)dct_fast_kernel<MODE, true, true> : (void*)dct_fast_kernel<MODE, false, true>;
+    return contig ? (void*)dct_fast_kernel<MODE, true, false> : (void*)dct_fast_kernel<MODE, false, false>;
+}
+
+static void* select_dct(int mode, int elem_bytes, bool contig, bool batched, bool fast)
+{
+    if (fast) {
+        if (mode == DCT_FWD) return dct_fast<DCT_FWD>(contig, batched);
+        if (mode == DCT_MID) return dct_fast<DCT_MID>(contig, batched);
+        return dct_fast<DCT_INV>(contig, batched);
+    }
     if (elem_bytes == 4) {
         if (mode == DCT_FWD) return dct_kernel<float, DCT_FWD>(contig, batched);
         if (mode == DCT_MID) return dct_kernel<float, DCT_MID>(contig, batched);
@@ -508,7 +889,7 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
     DctArgs<T> a;
     bfm_status s = make_dct_args<T>(g, axis, p, tabs, in, base, out, upd, sigma, part, done, &a);
     if (s != BFM_OK) return s;
-    void* k = select_dct(mode, (int)sizeof(T), axis == 0, false);
+    void* k = select_dct(mode, (int)sizeof(T), axis == 0, false, p.fast != 0);
     BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int blocks = dct_blocks(p);
     const DctArgs<T>* none = nullptr;
@@ -538,7 +919,7 @@ bfm_status launch_dct_pass_batched(const Grid& g, int axis, int mode, int nprob,
                                    const void* dev_args, cudaStream_t st)
 {
     DctPlan p = plan_dct_pass(g, axis, (int)sizeof(T));
-    void* k = select_dct(mode, (int)sizeof(T), axis == 0, true);
+    void* k = select_dct(mode, (int)sizeof(T), axis == 0, true, p.fast != 0);
     BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int blocks = dct_blocks(p);
     DctArgs<T> dummy;

@@ -6,7 +6,7 @@
 namespace bfm {
 
 struct CtPlan {
-    int K, G, W, LD, LDI, threads;
+    int K, G, W, LD, LDI, LDH, threads;
     size_t smem;
     LineTiles tiles;
 };
@@ -27,6 +27,7 @@ struct AxisTables {
 
 struct DctPlan {
     int G, W, LDZ, threads;
+    int fast;                 // FP32 power-of-two line: register Stockham kernel
     size_t smem;
     LineTiles tiles;
 };
