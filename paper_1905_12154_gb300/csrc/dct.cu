@@ -519,29 +519,48 @@ __global__ void __launch_bounds__(512, 1) dct_fast_kernel(DctArgs<float> a0, con
         const Tile tl = tile_at(lt, tile);
         const int np = (tl.wact + 1) / 2;
         const bool active = (pp < np);
-        // ---- load: natural order of the reordered sequence (FWD/MID) or spectrum (INV)
+        // ---- load: natural order of the reordered sequence (FWD/MID) or spectrum (INV).
+        // Each thread issues U independent loads before storing any, so a tile's
+        // loads overlap instead of forming a chain of memory latencies.
         {
+            constexpr int U = 4;
             const int np_pow = CONTIG ? 1 : (1 << a.lnp);
             const int per = CONTIG ? n : np_pow * n;
             const int reps = CONTIG ? np : 1;
+            const int bd = blockDim.x;
             for (int q0 = 0; q0 < reps; ++q0)
-            for (int e = tid; e < per; e += blockDim.x) {
-                int q, j;
-                if (CONTIG) { q = q0; j = e; }
-                else        { q = e & (np_pow - 1); j = e >> a.lnp; }
-                if (q >= np) continue;
-                const int lb = 2 * q + 1;
-                const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
-                T xa = a.in[ada];
-                T xb = (T)0;
-                if (lb < tl.wact) xb = a.in[ada + tl.lstride];
-                if (MODE == DCT_FWD && a.base) {
-                    xa = a.base[ada] - xa;
-                    if (lb < tl.wact) xb = a.base[ada + tl.lstride] - xb;
+            for (int e0 = tid; e0 < per; e0 += U * bd) {
+                T xa[U], xb[U], ba[U], bb[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * bd;
+                    xa[u] = xb[u] = ba[u] = bb[u] = (T)0;
+                    int q, j;
+                    if (CONTIG) { q = q0; j = e; } else { q = e & (np_pow - 1); j = e >> a.lnp; }
+                    if (e < per && q < np) {
+                        const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                        const bool hb = (2 * q + 1 < tl.wact);
+                        xa[u] = a.in[ada];
+                        if (hb) xb[u] = a.in[ada + tl.lstride];
+                        if (MODE == DCT_FWD && a.base) {
+                            ba[u] = a.base[ada];
+                            if (hb) bb[u] = a.base[ada + tl.lstride];
+                        }
+                    }
                 }
-                C v; v.x = xa; v.y = xb;
-                const int m = (MODE == DCT_INV) ? j : ((j & 1) ? (n - 1 - (j >> 1)) : (j >> 1));
-                zs[(size_t)q * a.LDZ + padix(m)] = v;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * bd;
+                    int q, j;
+                    if (CONTIG) { q = q0; j = e; } else { q = e & (np_pow - 1); j = e >> a.lnp; }
+                    if (e < per && q < np) {
+                        C v;
+                        if (MODE == DCT_FWD && a.base) { v.x = ba[u] - xa[u]; v.y = bb[u] - xb[u]; }
+                        else { v.x = xa[u]; v.y = xb[u]; }
+                        const int m = (MODE == DCT_INV) ? j : ((j & 1) ? (n - 1 - (j >> 1)) : (j >> 1));
+                        zs[(size_t)q * a.LDZ + padix(m)] = v;
+                    }
+                }
             }
         }
         __syncthreads();
@@ -621,34 +640,54 @@ __global__ void __launch_bounds__(512, 1) dct_fast_kernel(DctArgs<float> a0, con
             __syncthreads();
             stockham_fft<+1>(z, n, t, G, active, a.tw, a.fnst, a.frad);
         }
-        // ---- store ------------------------------------------------------------------
+        // ---- store (the potential update reads its U values first) ------------------
         {
+            constexpr int U = 4;
             const int np_pow = CONTIG ? 1 : (1 << a.lnp);
             const int per = CONTIG ? n : np_pow * n;
             const int reps = CONTIG ? np : 1;
+            const int bd = blockDim.x;
             for (int q0 = 0; q0 < reps; ++q0)
-            for (int e = tid; e < per; e += blockDim.x) {
-                int q, j;
-                if (CONTIG) { q = q0; j = e; }
-                else        { q = e & (np_pow - 1); j = e >> a.lnp; }
-                if (q >= np) continue;
-                const int lb = 2 * q + 1;
-                const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
-                C v;
-                if (MODE == DCT_FWD) {
-                    v = zs[(size_t)q * a.LDZ + padix(j)];
-                } else {
-                    const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
-                    v = zs[(size_t)q * a.LDZ + padix(m)];
-                    v.x *= inv_n;
-                    v.y *= inv_n;
-                }
+            for (int e0 = tid; e0 < per; e0 += U * bd) {
+                T ua[U], ub[U];
                 if (MODE == DCT_INV && a.upd) {
-                    a.out[ada] = a.upd[ada] + sig * v.x;
-                    if (lb < tl.wact) a.out[ada + tl.lstride] = a.upd[ada + tl.lstride] + sig * v.y;
-                } else {
-                    a.out[ada] = v.x;
-                    if (lb < tl.wact) a.out[ada + tl.lstride] = v.y;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int e = e0 + u * bd;
+                        ua[u] = ub[u] = (T)0;
+                        int q, j;
+                        if (CONTIG) { q = q0; j = e; } else { q = e & (np_pow - 1); j = e >> a.lnp; }
+                        if (e < per && q < np) {
+                            const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                            ua[u] = a.upd[ada];
+                            if (2 * q + 1 < tl.wact) ub[u] = a.upd[ada + tl.lstride];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * bd;
+                    int q, j;
+                    if (CONTIG) { q = q0; j = e; } else { q = e & (np_pow - 1); j = e >> a.lnp; }
+                    if (e >= per || q >= np) continue;
+                    const int lb = 2 * q + 1;
+                    const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                    C v;
+                    if (MODE == DCT_FWD) {
+                        v = zs[(size_t)q * a.LDZ + padix(j)];
+                    } else {
+                        const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
+                        v = zs[(size_t)q * a.LDZ + padix(m)];
+                        v.x *= inv_n;
+                        v.y *= inv_n;
+                    }
+                    if (MODE == DCT_INV && a.upd) {
+                        a.out[ada] = ua[u] + sig * v.x;
+                        if (lb < tl.wact) a.out[ada + tl.lstride] = ub[u] + sig * v.y;
+                    } else {
+                        a.out[ada] = v.x;
+                        if (lb < tl.wact) a.out[ada + tl.lstride] = v.y;
+                    }
                 }
             }
         }
