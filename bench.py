@@ -45,6 +45,15 @@ BYTES_PER_CELL_2D = {
     "dct_inv": 12,         # read spectrum, read potential, write potential
     "pushforward": 16,     # zero rho, read psi, read mu, write rho
 }
+# Long columns (4096^2): the axis-1 sweeps run along the rows of a transposed
+# copy.  The row sweep then reads and writes (8 bytes); the dual dot of the
+# c-transform output moves into the transpose back, so of the 12 transposes of
+# an iteration 4 read a weight as well (8 x 8 + 4 x 12 bytes).
+BYTES_PER_CELL_2D_TRANSPOSED = dict(BYTES_PER_CELL_2D, ct_pass_axis1=8,
+                                    transpose=(8 * 8 + 4 * 12) / 12)
+# the method's own traffic per iteration (4 c-transforms of two sweeps, 2
+# Poisson solves of three sweeps, 2 pushforwards); transposes are not part of it
+METHOD_BYTES_PER_CELL_ITER = 4 * (12 + 12) + 2 * (12 + 8 + 12) + 2 * 16
 
 
 def peaks():
@@ -281,17 +290,18 @@ def main():
     pk, src = peaks()
     kinds = {k: v for k, v in prof.items() if not k.startswith("_")}
     launches = sum(c for _, c in kinds.values())
-    dom = max((k for k in kinds if k in BYTES_PER_CELL_2D), key=lambda k: kinds[k][0])
+    table = BYTES_PER_CELL_2D_TRANSPOSED if kinds.get("transpose", (0, 0))[1] else BYTES_PER_CELL_2D
+    dom = max((k for k in kinds if k in table and kinds[k][1]), key=lambda k: kinds[k][0])
     ms, cnt = kinds[dom]
-    bytes_per_launch = BYTES_PER_CELL_2D[dom] * N
+    bytes_per_launch = table[dom] * N
     achieved = bytes_per_launch / (ms / cnt / 1e3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
             "bytes_per_launch": bytes_per_launch, "avg_launch_ms": ms / cnt}
-    total_alg = sum(BYTES_PER_CELL_2D.get(k, 0) * N * c for k, (m, c) in kinds.items())
-    per_iter = {"alg_bytes_per_iter": total_alg / args.steps,
-                "hbm_frac_per_iter": (total_alg / elapsed * ws / ws) / 1e9 / pk["hbm_gbs"] if ws == 1 else None}
+    alg_iter = METHOD_BYTES_PER_CELL_ITER * N
+    per_iter = {"alg_bytes_per_iter": alg_iter,
+                "hbm_frac_per_iter": alg_iter * args.steps / elapsed / 1e9 / pk["hbm_gbs"]}
     breakdown = {k: {"ms_per_iter": m / args.steps, "launches_per_iter": c / args.steps,
                      "share": m / max(sum(x for x, _ in kinds.values()), 1e-12)}
                  for k, (m, c) in kinds.items() if c}

@@ -165,6 +165,8 @@ __device__ __forceinline__ void line_sync(int w, int G)
     else asm volatile("bar.sync %0, %1;" :: "r"(1 + w), "r"(G) : "memory");
 }
 
+constexpr int kU = 4;      // column-tile loads each thread keeps in flight
+
 // BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
 template <typename T, int K, bool CONTIG, bool BATCHED>
 __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtArgs<T>* batch)
@@ -235,14 +237,29 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
                 }
             }
         } else {
+            // a column tile reads W neighbouring floats per row, so every
+            // thread keeps kU loads in flight before storing any of them
             const int total = n << a.lw;
-            for (int e = tid; e < total; e += blockDim.x) {
-                const int p = e >> a.lw, ww = e & (W - 1);
-                if (ww < tl.wact) {
+            const int nt = blockDim.x;
+            for (int e0 = tid; e0 < total; e0 += kU * nt) {
+                T v[kU], u[kU];
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int e = e0 + k * nt;
+                    const int p = e >> a.lw, ww = e & (W - 1);
+                    const bool ok = e < total && ww < tl.wact;
                     const long long ad = tl.base0 + ww + (long long)p * lt.es;
-                    const T v = a.in[ad];
-                    if (a.w_in) acc_t_in.add_prod(v, a.w_in[ad]);
-                    fs[(size_t)ww * a.LD + SK::f(p)] = a.negate ? -v : v;
+                    v[k] = ok ? a.in[ad] : (T)0;
+                    u[k] = (ok && a.w_in) ? a.w_in[ad] : (T)0;
+                }
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int e = e0 + k * nt;
+                    const int p = e >> a.lw, ww = e & (W - 1);
+                    if (e < total && ww < tl.wact) {
+                        if (a.w_in) acc_t_in.add_prod(v[k], u[k]);
+                        fs[(size_t)ww * a.LD + SK::f(p)] = a.negate ? -v[k] : v[k];
+                    }
                 }
             }
         }
@@ -373,13 +390,28 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
             }
         } else {
             const int total = n << a.lw;
-            for (int e = tid; e < total; e += blockDim.x) {
-                const int p = e >> a.lw, ww = e & (W - 1);
-                if (ww < tl.wact) {
-                    const long long ad = tl.base0 + ww + (long long)p * lt.es;
-                    const T v = fs[(size_t)ww * a.LD + SK::f(p)];
-                    a.out[ad] = v;
-                    if (a.w_out) acc_t_out.add_prod(v, a.w_out[ad]);
+            const int nt = blockDim.x;
+            for (int e0 = tid; e0 < total; e0 += kU * nt) {
+                T u[kU];
+                if (a.w_out) {
+#pragma unroll
+                    for (int k = 0; k < kU; ++k) {
+                        const int e = e0 + k * nt;
+                        const int p = e >> a.lw, ww = e & (W - 1);
+                        const long long ad = tl.base0 + ww + (long long)p * lt.es;
+                        u[k] = (e < total && ww < tl.wact) ? a.w_out[ad] : (T)0;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int e = e0 + k * nt;
+                    const int p = e >> a.lw, ww = e & (W - 1);
+                    if (e < total && ww < tl.wact) {
+                        const long long ad = tl.base0 + ww + (long long)p * lt.es;
+                        const T v = fs[(size_t)ww * a.LD + SK::f(p)];
+                        a.out[ad] = v;
+                        if (a.w_out) acc_t_out.add_prod(v, u[k]);
+                    }
                 }
             }
         }

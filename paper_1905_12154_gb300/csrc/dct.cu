@@ -203,7 +203,9 @@ dct_pass_kernel(DctArgs<T> a0, const DctArgs<T>* batch)
         if (MODE == DCT_MID) {
             // ---- divide by the eigenvalues; G = (1/N^2) sum w X^2 / lambda ------------
             if (active) {
-                const int ia = tl.i0 + 2 * pp, ib = ia + 1;
+                // index of the line along the other axis: the row of a row tile,
+                // else the axis-0 position of an interleaved tile
+                const int ia = (CONTIG ? (int)tl.outer : tl.i0) + 2 * pp, ib = ia + 1;
                 const bool has_b = (2 * pp + 1 < tl.wact);
                 T La = a.lam_a0[ia], Lb = has_b ? a.lam_a0[ib] : (T)0;
                 T wa = (ia == 0) ? (T)1 : (T)2, wb = (ib == 0) ? (T)1 : (T)2;
@@ -590,7 +592,9 @@ __global__ void __launch_bounds__(512, 1) dct_fast_kernel(DctArgs<float> a0, con
         }
         if (MODE == DCT_MID) {
             if (active) {
-                const int ia = tl.i0 + 2 * pp, ib = ia + 1;
+                // index of the line along the other axis: the row of a row tile,
+                // else the axis-0 position of an interleaved tile
+                const int ia = (CONTIG ? (int)tl.outer : tl.i0) + 2 * pp, ib = ia + 1;
                 const bool has_b = (2 * pp + 1 < tl.wact);
                 T La = a.lam_a0[ia], Lb = has_b ? a.lam_a0[ib] : (T)0;
                 T wa = (ia == 0) ? (T)1 : (T)2, wb = (ib == 0) ? (T)1 : (T)2;
@@ -849,8 +853,10 @@ static bfm_status make_dct_args(const Grid& g, int axis, const DctPlan& p, const
 {
     const AxisTables& tb = tabs[axis];
     // host-side guard: never launch with tables that do not describe this axis
+    // a MID pass along rows (2-D, axis 0) takes the line eigenvalues of axis 1
+    const int line_axis = (axis == 0) ? 1 : 0;
     if (tb.n != g.n[axis] || !tb.tw || !tb.dtw || !tb.drev || !tb.lam || tb.rs.nst < 1 ||
-        !tabs[0].lam || (g.ndim == 3 && !tabs[1].lam)) {
+        (g.ndim == 2 && !tabs[line_axis].lam) || (g.ndim == 3 && (!tabs[0].lam || !tabs[1].lam))) {
         set_last_error("internal: DCT tables do not match the grid");
         return BFM_ERR_INVALID_ARG;
     }
@@ -860,7 +866,7 @@ static bfm_status make_dct_args(const Grid& g, int axis, const DctPlan& p, const
     a->dtw = reinterpret_cast<const cx_t<T>*>(tb.dtw);
     a->drev = tb.drev;
     a->lam_axis = reinterpret_cast<const T*>(tb.lam);
-    a->lam_a0 = reinterpret_cast<const T*>(tabs[0].lam);
+    a->lam_a0 = reinterpret_cast<const T*>(g.ndim == 2 ? tabs[line_axis].lam : tabs[0].lam);
     a->lam_a1 = (g.ndim == 3) ? reinterpret_cast<const T*>(tabs[1].lam) : nullptr;
     a->lt = p.tiles;
     a->G = p.G;

@@ -95,6 +95,15 @@ template <typename T>
 bfm_status launch_pushforward_batched(int ndim, long long max_cells, int nprob,
                                       const void* dev_args, cudaStream_t st);
 
+// layout.cu: out (C rows of R elements) = transpose of in (R rows of C
+// elements); with w (laid out like out), one FP64 partial sum of out * w per CTA
+template <typename T>
+bfm_status launch_transpose(const T* in, T* out, int R, int C, const T* w, double* part,
+                            const int* done, cudaStream_t st, int* blocks_used);
+// true when axis-1 sweeps of this 2-D grid run as row sweeps of a transposed copy
+bool transposed_axis1(const Grid& g, int elem_bytes);
+Grid transposed_grid(const Grid& g);
+
 // solver.cu: the Poisson solve on an explicit scratch block
 size_t poisson_scratch_bytes(const Grid& g, int eb);
 bfm_status poisson_on_scratch(const void* f, void* g_out, const Grid& g, bfm_precision prec,

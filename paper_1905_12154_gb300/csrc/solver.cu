@@ -137,7 +137,7 @@ size_t poisson_bytes(const Grid& g, int eb)
 size_t solve_bytes(const Grid& g, int eb, int max_iter)
 {
     return poisson_bytes(g, eb) + up256(sizeof(double) * 3 * ((size_t)max_iter + 1)) +
-           4 * up256((size_t)eb * g.N);
+           (transposed_axis1(g, eb) ? 5 : 4) * up256((size_t)eb * g.N);
 }
 
 void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Workspace* w, bool fields)
@@ -158,8 +158,10 @@ void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Workspace* 
         w->nu_n = p; p += up256((size_t)eb * g.N);
         w->tmp = p;  p += up256((size_t)eb * g.N);
         w->rho = p;  p += up256((size_t)eb * g.N);
+        w->xt = nullptr;
+        if (transposed_axis1(g, eb)) { w->xt = p; p += up256((size_t)eb * g.N); }
     } else {
-        w->logs = nullptr; w->mu_n = w->nu_n = w->tmp = w->rho = nullptr;
+        w->logs = nullptr; w->mu_n = w->nu_n = w->tmp = w->rho = w->xt = nullptr;
     }
     w->bytes = (size_t)(p - base);
 }
@@ -190,11 +192,12 @@ double* slot(Workspace* w, int s) { return w->parts + (size_t)s * kMaxPartials; 
 // optional per-launch timing (bfm_profile_begin / bfm_profile_end)
 // ---------------------------------------------------------------------------
 enum {
-    PK_CT0 = 0, PK_CT1, PK_CT2, PK_DCT_FWD, PK_DCT_MID, PK_DCT_INV, PK_PUSH, PK_SMALL, PK_COUNT
+    PK_CT0 = 0, PK_CT1, PK_CT2, PK_DCT_FWD, PK_DCT_MID, PK_DCT_INV, PK_PUSH, PK_SMALL,
+    PK_TRANSPOSE, PK_COUNT
 };
 static const char* kProfNames[PK_COUNT] = {
     "ct_pass_axis0", "ct_pass_axis1", "ct_pass_axis2", "dct_fwd", "dct_mid", "dct_inv",
-    "pushforward", "reduce_step"};
+    "pushforward", "reduce_step", "transpose"};
 
 struct ProfRec { int kind; int launches; cudaEvent_t a, b; };
 struct Profiler {
@@ -222,12 +225,42 @@ struct ProfScope {
 // ---------------------------------------------------------------------------
 // the pieces of one half step
 // ---------------------------------------------------------------------------
-// c-transform out = src^c with the two dot products of the dual value.
+template <typename T>
+static bfm_status transpose(const Grid& g, bool forward, const T* in, T* out, const T* w,
+                            double* part, int* n_part, const int* done, cudaStream_t st)
+{
+    ProfScope ps(PK_TRANSPOSE, 1, st);
+    // forward: the n1 rows of n0 cells become n0 rows of n1 cells
+    const int R = forward ? g.n[1] : g.n[0], C = forward ? g.n[0] : g.n[1];
+    return launch_transpose<T>(in, out, R, C, w, part, done, st, n_part);
+}
+
+// c-transform out = src^c with the two dot products of the dual value.  With
+// xt (2-D, long columns) the axis-1 sweep runs along the rows of a transposed
+// copy and the dot product of the output is taken on the way back.
 template <typename T>
 static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_src, const T* w_out,
                                double* p_in, int* n_in, double* p_out, int* n_out, const int* done,
-                               cudaStream_t st)
+                               cudaStream_t st, T* xt)
 {
+    if (xt) {
+        bfm_status s;
+        {
+            ProfScope ps(PK_CT0, 1, st);
+            s = launch_ct_pass<T>(g, 0, src, out, true, w_src, p_in, nullptr, nullptr, done,
+                                  kMaxPartials, st, n_in);
+            if (s != BFM_OK) return s;
+        }
+        s = transpose<T>(g, true, out, xt, nullptr, nullptr, nullptr, done, st);
+        if (s != BFM_OK) return s;
+        {
+            ProfScope ps(PK_CT1, 1, st);
+            s = launch_ct_pass<T>(transposed_grid(g), 0, xt, xt, false, nullptr, nullptr, nullptr,
+                                  nullptr, done, kMaxPartials, st, nullptr);
+            if (s != BFM_OK) return s;
+        }
+        return transpose<T>(g, false, xt, out, w_out, p_out, n_out, done, st);
+    }
     for (int a = 0; a < g.ndim; ++a) {
         const bool first = (a == 0), last = (a == g.ndim - 1);
         int used = 0;
@@ -245,11 +278,32 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
 
 // Forward transforms of f = base - in up to (and including) the middle pass;
 // the spectrum of g stays in `buf`.  G partials go to p_g.
+// With xt (2-D, long columns) the middle pass runs along the rows of a
+// transposed copy.
 template <typename T>
 static bfm_status poisson_forward(const Grid& g, const AxisTables* tabs, const T* in,
                                   const T* base, T* buf, double* p_g, int* n_g, const int* done,
-                                  cudaStream_t st)
+                                  cudaStream_t st, T* xt)
 {
+    if (xt) {
+        bfm_status s;
+        {
+            ProfScope ps(PK_DCT_FWD, 1, st);
+            s = launch_dct_pass<T>(g, 0, PASS_FWD, tabs, in, base, buf, nullptr, nullptr, nullptr,
+                                   done, st, nullptr);
+            if (s != BFM_OK) return s;
+        }
+        s = transpose<T>(g, true, buf, xt, nullptr, nullptr, nullptr, done, st);
+        if (s != BFM_OK) return s;
+        {
+            ProfScope ps(PK_DCT_MID, 1, st);
+            const AxisTables swapped[3] = {tabs[1], tabs[0], tabs[2]};
+            s = launch_dct_pass<T>(transposed_grid(g), 0, PASS_MID, swapped, xt, nullptr, xt,
+                                   nullptr, nullptr, p_g, done, st, n_g);
+            if (s != BFM_OK) return s;
+        }
+        return transpose<T>(g, false, xt, buf, nullptr, nullptr, nullptr, done, st);
+    }
     const int last = g.ndim - 1;
     for (int a = 0; a < last; ++a) {
         ProfScope ps(PK_DCT_FWD, 1, st);
@@ -299,7 +353,8 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     const T* target = phi_half ? nu : mu;
     int ni = 0, no = 0, ng = 0;
     bfm_status s;
-    s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st);
+    T* xt = (T*)w->xt;
+    s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -312,7 +367,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
         s = launch_pushforward<T>(g, tmp, source, rho, done, st);
         if (s != BFM_OK) return s;
     }
-    s = poisson_forward<T>(g, w->tabs, rho, target, rho, slot(w, 2), &ng, done, st);
+    s = poisson_forward<T>(g, w->tabs, rho, target, rho, slot(w, 2), &ng, done, st, xt);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -321,7 +376,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     }
     s = poisson_inverse<T>(g, w->tabs, rho, src, src, &w->state->sigma, done, st);
     if (s != BFM_OK) return s;
-    s = ct_with_dots<T>(g, src, dst, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st);
+    s = ct_with_dots<T>(g, src, dst, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -396,7 +451,7 @@ bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int ma
     // ||nu - 1||^2_{H^-1}: the mean of nu/mass is 1 and the zero mode is dropped
     int ng = 0;
     s = poisson_forward<T>(g, w.tabs, (const T*)w.nu_n, nullptr, (T*)w.rho, slot(&w, 2), &ng,
-                           nullptr, st);
+                           nullptr, st, (T*)w.xt);
     if (s != BFM_OK) return s;
     Logs logs = logs_of(&w, max_iter);
     finalize_G_kernel<<<1, 256, 0, st>>>(w.state, slot(&w, 2), ng, 2, logs);
@@ -745,7 +800,7 @@ static bfm_status poisson_impl(const T* f, T* gout, const Grid& g, double* G_out
     bfm_status s = fill_tables<T>(g, &w, st);
     if (s != BFM_OK) return s;
     int ng = 0;
-    s = poisson_forward<T>(g, w.tabs, f, nullptr, gout, slot(&w, 2), &ng, nullptr, st);
+    s = poisson_forward<T>(g, w.tabs, f, nullptr, gout, slot(&w, 2), &ng, nullptr, st, (T*)nullptr);
     if (s != BFM_OK) return s;
     s = poisson_inverse<T>(g, w.tabs, gout, gout, nullptr, nullptr, nullptr, st);
     if (s != BFM_OK) return s;

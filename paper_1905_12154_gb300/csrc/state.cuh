@@ -44,6 +44,8 @@ struct Workspace {
     void* nu_n;
     void* tmp;
     void* rho;
+    void* xt;                 // transposed copy for axis-1 sweeps of 2-D grids with
+                              // long columns (transposed_axis1), else NULL
     size_t bytes;
 };
 

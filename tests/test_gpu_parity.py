@@ -270,5 +270,59 @@ def test_profiler_counts_launches(B):
     assert prof["pushforward"][1] == 4
     assert prof["dct_fwd"][1] == prof["dct_mid"][1] == prof["dct_inv"][1] == 4
     assert prof["reduce_step"][1] == 12
+    assert prof["transpose"][1] == 0          # short columns: interleaved column tiles
     assert prof["_dropped"][1] == 0
     assert all(v[0] > 0 for k, v in prof.items() if not k.startswith("_") and v[1])
+
+
+# --- long columns: axis-1 sweeps along the rows of a transposed copy ----------
+# A tile of neighbouring columns holds only a few lines when the columns are
+# long (from 1024 FP64 or 2048 FP32 cells), so 2-D grids with such columns
+# transpose the field, sweep rows and transpose back.  The grids below are
+# narrow (few columns) so that the oracle stays fast, and n0 is not a power
+# of two so the row sweeps of the original layout take the general DCT path.
+
+def long_column_pair(shape, seed):
+    rng = np.random.default_rng(seed)
+    mu = si.normalise(si.gaussian_mixture(shape, rng.uniform(0.3, 0.7, (2, 2)), [0.12, 0.08]))
+    nu = si.normalise(si.gaussian_mixture(shape, rng.uniform(0.3, 0.7, (3, 2)), [0.1, 0.1, 0.07]))
+    return mu, nu
+
+
+def test_solve_long_columns_fp64(B):
+    mu, nu = long_column_pair((48, 1024), 41)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=6)
+    r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=6)
+    assert r["iters"] == ref["iters"] == 6
+    assert np.max(np.abs(r["dual"] - ref["dual"])) < 1e-12
+    assert np.max(np.abs(r["resid"] - ref["resid"])) < 1e-9
+    assert np.max(np.abs(r["sigma"] - ref["sigma"])) < 1e-12
+    assert abs(r["w2sq"] - ref["w2sq"]) < 1e-12
+    assert np.max(np.abs(host(r["phi"]) - ref["phi"])) < 1e-10
+    assert np.max(np.abs(host(r["psi"]) - ref["psi"])) < 1e-10
+    assert np.max(np.abs(host(r["map"]) - ref["map"])) * 1024 < 1e-8    # in cells
+
+
+def test_solve_long_columns_fp32(B):
+    mu, nu = long_column_pair((24, 2048), 42)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=10)
+    r = B.bfm_solve(dev(mu, torch.float32), dev(nu, torch.float32), tol=0.0, max_iter=10)
+    assert r["iters"] == 10
+    assert abs(r["w2sq"] - ref["w2sq"]) / ref["w2sq"] < 1e-5
+    assert np.max(np.abs(r["resid"] - ref["resid"])) < 1e-3
+
+
+@pytest.mark.parametrize("shape,dt", [((48, 1024), torch.float64), ((24, 2048), torch.float32)],
+                         ids=["fp64", "fp32"])
+def test_long_columns_take_transposed_sweeps(B, shape, dt):
+    """Per iteration: 4 c-transforms and 2 Poisson solves, each with a
+    transpose before and after its axis-1 sweep."""
+    mu, nu = long_column_pair(shape, 43)
+    s = B.BfmSolver(dev(mu, dt), dev(nu, dt), tol=0.0, max_iter=10)
+    B.bfm_profile_begin(200)
+    s.iterate(1)
+    prof = B.bfm_profile_end()
+    assert prof["transpose"][1] == 12
+    assert prof["ct_pass_axis0"][1] == prof["ct_pass_axis1"][1] == 4
+    assert prof["dct_fwd"][1] == prof["dct_mid"][1] == prof["dct_inv"][1] == 2
+    assert prof["_dropped"][1] == 0
