@@ -47,6 +47,7 @@ struct CtArgs {
     int negate;           // the pass reads -in
     int vec4;             // rows may be moved as float4 (n % 4 == 0, 16-byte aligned)
     int lw;               // log2(W); interleaved tiles have W a power of two
+    int ioff;             // row kernel: byte offset of the int scratch in shared memory
 };
 
 // Shared-memory layout of a line: thread t owns cells [tK, tK+K).  Stored
@@ -55,7 +56,7 @@ struct CtArgs {
 // stacks) makes the per-thread stride odd, so the threads of a warp hit
 // distinct banks.
 template <int K> struct Skew {
-    static constexpr int lg = (K >= 16) ? 4 : (K >= 8) ? 3 : (K >= 4) ? 2 : (K >= 2) ? 1 : 0;
+    static constexpr int lg = (K >= 32) ? 5 : (K >= 16) ? 4 : (K >= 8) ? 3 : (K >= 4) ? 2 : (K >= 2) ? 1 : 0;
     __device__ __forceinline__ static int f(int p) { return p + (p >> lg); }
     __device__ __forceinline__ static int s(int p) { return p + 2 * (p >> lg); }
 };
@@ -430,6 +431,253 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
 }
 
 // ---------------------------------------------------------------------------
+// Row sweeps of long lines (axis 0, n >= kRowMinN): one group of G threads
+// per line, K = 32 cells per thread.  Compared with the tile kernel above:
+//   * lines are independent: each group takes rows g, g + groups, ... and
+//     synchronises only its own G threads, so no line waits for another;
+//   * shared memory holds only the line values (the stacks in place) and the
+//     stack indices, about 6.2 bytes per cell, so 8 lines of 4096 FP32 cells
+//     fit on an SM at 1024 threads;
+//   * the merged envelope is not compacted cell by cell: the owner of a
+//     thread's first output is found by binary search over the list of
+//     non-empty segments (each thread's surviving stack range), then inside
+//     one segment, and the sweep steps from segment to segment;
+//   * the outputs go from registers straight to global memory, four at a
+//     time (a thread's 32 outputs are one 128-byte line), fused with the dual
+//     dot product.
+// ---------------------------------------------------------------------------
+constexpr int kRowK = 32;
+constexpr int kRowMinN = 1024;
+
+// Barrier of one line group (G >= 32 threads, whole warps): a single warp
+// uses the warp barrier, larger groups named barrier 1 + w.
+__device__ __forceinline__ void group_sync(int w, int G)
+{
+    if (G == 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" :: "r"(1 + w), "r"(G) : "memory");
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
+{
+    if (a.done && *a.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using SK = Skew<K>;
+    const int n = a.lt.n;
+    const int G = a.G;
+    const int W = a.lt.W;                          // line groups per CTA
+    const long long nrows = a.lt.nlines;
+    T* fs = reinterpret_cast<T*>(smem_raw);
+    short* stk_all = reinterpret_cast<short*>(fs + (size_t)W * a.LD);
+    short* seg_all = stk_all + (size_t)W * a.LDI;  // per group: beg[G], end[G], nzs[G]
+    const int nwl = (G + 31) / 32;
+    int* wsum_all = reinterpret_cast<int*>(smem_raw + a.ioff);
+    int* cnt_all = wsum_all + W * nwl;
+    __shared__ double red[32];
+
+    const int tid = threadIdx.x;
+    const int w = tid / G, t = tid - w * G;
+    const int lane = tid & 31;
+    T* f = fs + (size_t)w * a.LD;
+    short* stk = stk_all + (size_t)w * a.LDI;
+    short* beg = seg_all + (size_t)w * 3 * G;
+    short* end = beg + G;
+    short* nzs = end + G;
+    int* wsum = wsum_all + w * nwl;
+    const T hh = a.hh;
+    const int lo = t * K;
+    const int hi = min(lo + K, n);
+    Acc<T> acc_t_in, acc_t_out;
+    double acc_in = 0.0, acc_out = 0.0;
+    const long long groups = (long long)gridDim.x * W;
+
+    for (long long row = (long long)blockIdx.x * W + w; row < nrows; row += groups) {
+        const long long rb = row * n;
+        // ---- load: the group reads its row with coalesced loads, kU at a time ----
+        if (sizeof(T) == 4 && a.vec4) {
+            const float4* src = reinterpret_cast<const float4*>(a.in + rb);
+            const float4* wsrc = reinterpret_cast<const float4*>(a.w_in + rb);
+            const int nq = n >> 2;
+            for (int q0 = t; q0 < nq; q0 += kU * G) {
+                float4 v[kU], u[kU];
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int q = q0 + k * G;
+                    v[k] = q < nq ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    u[k] = (q < nq && a.w_in) ? wsrc[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int q = q0 + k * G;
+                    if (q < nq) {
+                        float4 x = v[k];
+                        if (a.w_in) {
+                            acc_t_in.add_prod(x.x, u[k].x); acc_t_in.add_prod(x.y, u[k].y);
+                            acc_t_in.add_prod(x.z, u[k].z); acc_t_in.add_prod(x.w, u[k].w);
+                        }
+                        if (a.negate) { x.x = -x.x; x.y = -x.y; x.z = -x.z; x.w = -x.w; }
+                        f[SK::f(4 * q)] = x.x;     f[SK::f(4 * q + 1)] = x.y;
+                        f[SK::f(4 * q + 2)] = x.z; f[SK::f(4 * q + 3)] = x.w;
+                    }
+                }
+            }
+        } else {
+            for (int p0 = t; p0 < n; p0 += kU * G) {
+                T v[kU], u[kU];
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int p = p0 + k * G;
+                    v[k] = p < n ? a.in[rb + p] : (T)0;
+                    u[k] = (p < n && a.w_in) ? a.w_in[rb + p] : (T)0;
+                }
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int p = p0 + k * G;
+                    if (p < n) {
+                        if (a.w_in) acc_t_in.add_prod(v[k], u[k]);
+                        f[SK::f(p)] = a.negate ? -v[k] : v[k];
+                    }
+                }
+            }
+        }
+        group_sync(w, G);
+        // ---- A: envelope of this thread's chunk (stack in place) -------------
+        if (lo < n) {
+            int top = lo;
+            int s1 = lo, s0 = -1;
+            T v1 = f[SK::f(lo)], v0 = (T)0;
+            stk[SK::s(lo)] = (short)lo;
+            for (int q = lo + 1; q < hi; ++q) {
+                const T vq = f[SK::f(q)];
+                while (s0 >= 0 && hidden_v(s0, v0, s1, v1, q, vq, hh)) {
+                    --top;
+                    s1 = s0; v1 = v0;
+                    if (top > lo) { s0 = stk[SK::s(top - 1)]; v0 = f[SK::f(top - 1)]; }
+                    else s0 = -1;
+                }
+                ++top;
+                stk[SK::s(top)] = (short)q;
+                f[SK::f(top)] = vq;
+                s0 = s1; v0 = v1;
+                s1 = q; v1 = vq;
+            }
+            beg[t] = (short)lo;
+            end[t] = (short)(top + 1);
+        } else {
+            beg[t] = 0;
+            end[t] = 0;
+        }
+        group_sync(w, G);
+        // ---- B: pairwise merges ----------------------------------------------
+        for (int s = 1; s < G; s <<= 1) {
+            if ((t & (2 * s - 1)) == 0 && t + s < G) merge_pair<K>(f, stk, beg, end, t, s, n, hh);
+            if (4 * s <= 32) __syncwarp();
+            else group_sync(w, G);
+        }
+        group_sync(w, G);
+        // ---- C: list of non-empty segments, in order ---------------------------
+        {
+            const bool ne = end[t] > beg[t];
+            // groups are whole warps (G >= 32)
+            const unsigned mine = __ballot_sync(0xffffffffu, ne);
+            int pos = __popc(mine & ((1u << lane) - 1u));
+            if (G > 32) {
+                if (lane == 0) wsum[t >> 5] = __popc(mine);
+                group_sync(w, G);
+                for (int i = 0; i < (t >> 5); ++i) pos += wsum[i];
+            }
+            if (ne) nzs[pos] = (short)t;
+            if (t == G - 1) cnt_all[w] = pos + (ne ? 1 : 0);
+        }
+        group_sync(w, G);
+        // ---- D: evaluate this thread's outputs, store, dual dot ----------------
+        if (lo < n) {
+            const int M = cnt_all[w];
+            int ml = 0, mh = M - 1;
+            while (ml < mh) {
+                const int mid = (ml + mh + 1) >> 1;
+                const int pu = beg[nzs[mid]], pv = end[nzs[mid - 1]] - 1;
+                if (parab(hh, lo, (int)stk[SK::s(pu)], f[SK::f(pu)]) <
+                    parab(hh, lo, (int)stk[SK::s(pv)], f[SK::f(pv)])) ml = mid;
+                else mh = mid - 1;
+            }
+            const int m = ml;
+            const int pe = end[nzs[m]];
+            int pl = beg[nzs[m]], ph = pe - 1;
+            while (pl < ph) {
+                const int mid = (pl + ph + 1) >> 1;
+                if (parab(hh, lo, (int)stk[SK::s(mid)], f[SK::f(mid)]) <
+                    parab(hh, lo, (int)stk[SK::s(mid - 1)], f[SK::f(mid - 1)])) pl = mid;
+                else ph = mid - 1;
+            }
+            int jc = stk[SK::s(pl)];
+            T fc = f[SK::f(pl)];
+            // the parabola after the current one on the envelope: the next
+            // position of its segment, else the first of the next non-empty
+            // segment; (mn, pen) are the list index and end of pn's segment
+            int pn = pl + 1, mn = m, pen = pe;
+            if (pn >= pe) {
+                mn = m + 1;
+                if (mn < M) { pn = beg[nzs[mn]]; pen = end[nzs[mn]]; } else pn = -1;
+            }
+            int jn = -1;
+            T fn = (T)0;
+            if (pn >= 0) { jn = stk[SK::s(pn)]; fn = f[SK::f(pn)]; }
+            T* dst = a.out + rb;
+            const T* wo = a.w_out ? a.w_out + rb : nullptr;
+            for (int x0 = lo; x0 < hi; x0 += 4) {
+                T o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int x = x0 + k;
+                    T vc = parab(hh, x, jc, fc);
+                    while (jn >= 0) {
+                        const T vn = parab(hh, x, jn, fn);
+                        if (!(vn <= vc)) break;
+                        jc = jn; fc = fn; vc = vn;           // advance to pn
+                        if (pn + 1 < pen) ++pn;
+                        else {
+                            ++mn;
+                            if (mn < M) { pn = beg[nzs[mn]]; pen = end[nzs[mn]]; } else pn = -1;
+                        }
+                        if (pn >= 0) { jn = stk[SK::s(pn)]; fn = f[SK::f(pn)]; } else jn = -1;
+                    }
+                    o[k] = vc;
+                }
+                if (sizeof(T) == 4 && a.vec4 && x0 + 4 <= hi) {
+                    float4 v4 = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
+                    *reinterpret_cast<float4*>(dst + x0) = v4;
+                    if (wo) {
+                        const float4 u4 = *reinterpret_cast<const float4*>(wo + x0);
+                        acc_t_out.add_prod(o[0], (T)u4.x); acc_t_out.add_prod(o[1], (T)u4.y);
+                        acc_t_out.add_prod(o[2], (T)u4.z); acc_t_out.add_prod(o[3], (T)u4.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (x0 + k < hi) {
+                            dst[x0 + k] = o[k];
+                            if (wo) acc_t_out.add_prod(o[k], wo[x0 + k]);
+                        }
+                    }
+                }
+            }
+        }
+        acc_in += acc_t_in.take();
+        acc_out += acc_t_out.take();
+        group_sync(w, G);            // the next row overwrites this group's arrays
+    }
+    if (a.part_in) {
+        const double s = block_sum(acc_in, red);
+        if (threadIdx.x == 0) a.part_in[blockIdx.x] = s;
+    }
+    if (a.part_out) {
+        const double s = block_sum(acc_out, red);
+        if (threadIdx.x == 0) a.part_out[blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -537,6 +785,39 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
     return p;
 }
 
+static bool use_row_kernel(const Grid& g, int axis) { return axis == 0 && g.n[0] >= kRowMinN; }
+
+// Row kernel plan: K = 32 cells per thread, G = the next power of two of
+// n / 32 (at least 32, so every group is whole warps), as many groups per
+// CTA as fit 512 threads and about 110 KB (two CTAs per SM).
+static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
+{
+    CtPlan p;
+    const int n = g.n[0];
+    p.K = kRowK;
+    p.G = next_pow2((n + p.K - 1) / p.K);
+    const int chunks = (n + p.K - 1) / p.K + 1;
+    p.LD = n + chunks + 2;
+    p.LD += p.LD & 1;
+    p.LDI = n + 2 * chunks + 8;
+    p.LDI += p.LDI & 1;
+    const int nwl = (p.G + 31) / 32;
+    const size_t line_bytes = (size_t)p.LD * elem_bytes + (size_t)p.LDI * 2 + 3 * (size_t)p.G * 2 +
+                              4 * (size_t)nwl + 4;
+    int W = 512 / p.G;
+    if (W < 1) W = 1;
+    while (W > 1 && (size_t)W * line_bytes > 110 * 1024) --W;
+    p.W = W;
+    size_t off = (size_t)W * p.LD * elem_bytes + (size_t)W * p.LDI * 2 + (size_t)W * 3 * p.G * 2;
+    off = (off + 15) & ~(size_t)15;
+    p.ioff = (int)off;
+    p.LDH = 0;
+    p.smem = off + (size_t)W * nwl * 4 + (size_t)W * 4 + 16;
+    p.threads = W * p.G;
+    p.tiles = make_tiles(g, 0, W);
+    return p;
+}
+
 template <typename T>
 static CtArgs<T> make_ct_args(const Grid& g, int axis, const CtPlan& p, const T* in, T* out,
                               bool negate, const T* w_in, double* part_in, const T* w_out,
@@ -553,6 +834,7 @@ static CtArgs<T> make_ct_args(const Grid& g, int axis, const CtPlan& p, const T*
     a.vec4 = (axis == 0 && g.n[0] % 4 == 0 && al16(in) && al16(out) && al16(w_in) && al16(w_out)) ? 1 : 0;
     a.lw = 0;
     while ((1 << a.lw) < p.W) ++a.lw;
+    a.ioff = p.ioff;
     return a;
 }
 
@@ -571,6 +853,22 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
                           const T* w_in, double* part_in, const T* w_out, double* part_out,
                           const int* done, int max_blocks, cudaStream_t st, int* blocks_used)
 {
+    if (use_row_kernel(g, axis)) {
+        CtPlan p = plan_ct_row(g, (int)sizeof(T));
+        CtArgs<T> a = make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out,
+                                      done);
+        void* k = (void*)ct_row_kernel<T, kRowK>;
+        BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+        long long blocks = (p.tiles.nlines + p.W - 1) / p.W;
+        const long long cap = (long long)num_sms() * 2;      // two resident CTAs per SM
+        if (blocks > cap) blocks = cap;
+        if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
+        if (blocks < 1) blocks = 1;
+        void* args[] = {&a};
+        BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(p.threads), args, p.smem, st));
+        if (blocks_used) *blocks_used = (int)blocks;
+        return BFM_OK;
+    }
     CtPlan p = plan_ct_pass(g, axis, (int)sizeof(T));
     CtArgs<T> a = make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out, done);
     void* k = select_kernel<T>(p.K, axis == 0, false);

@@ -7,6 +7,7 @@ namespace bfm {
 
 struct CtPlan {
     int K, G, W, LD, LDI, LDH, threads;
+    int ioff = 0;             // row kernel: byte offset of the int scratch
     size_t smem;
     LineTiles tiles;
 };

@@ -40,7 +40,10 @@ def host(t):
     return t.detach().double().cpu().numpy()
 
 
-CT_SHAPES = [(2, 2), (7, 5), (64, 64), (33, 100), (257, 96), (48, 31, 20), (9, 40, 13)]
+# rows of 1024 cells or more take the row kernel (32 cells per thread, one
+# thread group per row): aligned, ragged (1500) and unaligned (1027) lengths
+CT_SHAPES = [(2, 2), (7, 5), (64, 64), (33, 100), (257, 96), (48, 31, 20), (9, 40, 13),
+             (1024, 3), (1500, 4), (1027, 3), (4096, 2)]
 
 
 @pytest.mark.parametrize("shape", CT_SHAPES, ids=str)
@@ -73,6 +76,15 @@ def test_ctransform_in_place_and_invariants(B):
     x = c1.clone()
     B.bfm_ctransform(x, out=x)                      # in place
     assert torch.equal(x, c2)
+
+
+def test_ctransform_long_rows_in_place(B):
+    """The row kernel reads a whole row before writing it: in place equals out of place."""
+    phi = dev(si.smooth_potential((5, 2048), 11, 0.2) + 0.01 * si.random_field((2048, 5), 11))
+    c1 = B.bfm_ctransform(phi)
+    x = phi.clone()
+    B.bfm_ctransform(x, out=x)
+    assert torch.equal(x, c1)
 
 
 POISSON_SHAPES = [(2, 3), (16, 12), (64, 48), (96, 128), (27, 32), (384, 8), (12, 18, 16),
