@@ -430,6 +430,86 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
     }
 }
 
+// Parabola indices held in T: differences of indices below 2^24 are exact in
+// FP32, so these give the same values as the integer forms above while
+// avoiding integer-to-float conversions (a fraction of the FP32 rate).
+template <typename T>
+__device__ __forceinline__ bool hidden_t(T a, T fa, T b, T fb, T c, T fc, T hh)
+{
+    const T lhs = (fb - fa) * (c - b) - (fc - fb) * (b - a);
+    const T rhs = hh * (c - a) * (b - a) * (c - b);
+    return lhs >= rhs;
+}
+
+template <typename T>
+__device__ __forceinline__ T parab_t(T hh, T x, T j, T fj)
+{
+    const T d = x - j;
+    return fma(hh, d * d, fj);
+}
+
+// merge_pair with the cached end parabolas' indices held in T
+template <int K, typename T>
+__device__ void merge_pair_t(const T* f, const short* stk, short* beg, short* end,
+                             int t, int s, int n, T hh)
+{
+    using SK = Skew<K>;
+    const int tl = t, tm = t + s, tr = t + 2 * s;
+    int lt = tm - 1;
+    while (lt >= tl && beg[lt] == end[lt]) --lt;
+    int rt = tm;
+    while (rt < tr && beg[rt] == end[rt]) ++rt;
+    if (lt < tl || rt >= tr) return;
+    int pb = end[lt] - 1;
+    int la = lt, pa = pb - 1, begla = beg[lt];
+    if (pa < begla) {
+        la = lt - 1;
+        while (la >= tl && beg[la] == end[la]) --la;
+        if (la >= tl) { pa = end[la] - 1; begla = beg[la]; } else pa = -1;
+    }
+    int pc = beg[rt];
+    int rd = rt, pd = pc + 1, endrd = end[rt];
+    if (pd >= endrd) {
+        rd = rt + 1;
+        while (rd < tr && beg[rd] == end[rd]) ++rd;
+        if (rd < tr) { pd = beg[rd]; endrd = end[rd]; } else pd = -1;
+    }
+    T ib = (T)stk[SK::s(pb)], ic = (T)stk[SK::s(pc)];
+    T fb = f[SK::f(pb)], fc = f[SK::f(pc)];
+    T ia = (T)0, id = (T)0, fa = (T)0, fd = (T)0;
+    if (pa >= 0) { ia = (T)stk[SK::s(pa)]; fa = f[SK::f(pa)]; }
+    if (pd >= 0) { id = (T)stk[SK::s(pd)]; fd = f[SK::f(pd)]; }
+    for (int guard = 0; guard <= n + 2; ++guard) {
+        if (pa >= 0 && hidden_t(ia, fa, ib, fb, ic, fc, hh)) {
+            if (la != lt) { end[lt] = beg[lt]; lt = la; }
+            pb = pa; ib = ia; fb = fa;
+            pa = pa - 1;
+            if (pa < begla) {
+                la = la - 1;
+                while (la >= tl && beg[la] == end[la]) --la;
+                if (la >= tl) { pa = end[la] - 1; begla = beg[la]; } else pa = -1;
+            }
+            if (pa >= 0) { ia = (T)stk[SK::s(pa)]; fa = f[SK::f(pa)]; }
+            continue;
+        }
+        if (pd >= 0 && hidden_t(ib, fb, ic, fc, id, fd, hh)) {
+            if (rd != rt) { beg[rt] = end[rt]; rt = rd; }
+            pc = pd; ic = id; fc = fd;
+            pd = pd + 1;
+            if (pd >= endrd) {
+                rd = rd + 1;
+                while (rd < tr && beg[rd] == end[rd]) ++rd;
+                if (rd < tr) { pd = beg[rd]; endrd = end[rd]; } else pd = -1;
+            }
+            if (pd >= 0) { id = (T)stk[SK::s(pd)]; fd = f[SK::f(pd)]; }
+            continue;
+        }
+        break;
+    }
+    end[lt] = (short)(pb + 1);
+    beg[rt] = (short)pc;
+}
+
 // ---------------------------------------------------------------------------
 // Row sweeps of long lines (axis 0, n >= kRowMinN): one group of G threads
 // per line, K = 32 cells per thread.  Compared with the tile kernel above:
@@ -498,16 +578,17 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
             const float4* src = reinterpret_cast<const float4*>(a.in + rb);
             const float4* wsrc = reinterpret_cast<const float4*>(a.w_in + rb);
             const int nq = n >> 2;
-            for (int q0 = t; q0 < nq; q0 += kU * G) {
-                float4 v[kU], u[kU];
+            constexpr int U = 2;                   // float4 pairs in flight (registers)
+            for (int q0 = t; q0 < nq; q0 += U * G) {
+                float4 v[U], u[U];
 #pragma unroll
-                for (int k = 0; k < kU; ++k) {
+                for (int k = 0; k < U; ++k) {
                     const int q = q0 + k * G;
                     v[k] = q < nq ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
                     u[k] = (q < nq && a.w_in) ? wsrc[q] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
-                for (int k = 0; k < kU; ++k) {
+                for (int k = 0; k < U; ++k) {
                     const int q = q0 + k * G;
                     if (q < nq) {
                         float4 x = v[k];
@@ -542,27 +623,34 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
         }
         group_sync(w, G);
         // ---- A: envelope of this thread's chunk (stack in place) -------------
+        // A chunk of K = 2^lg cells lies inside one skew block, so its cells
+        // are consecutive from fl / sl.
         if (lo < n) {
-            int top = lo;
-            int s1 = lo, s0 = -1;
-            T v1 = f[SK::f(lo)], v0 = (T)0;
-            stk[SK::s(lo)] = (short)lo;
-            for (int q = lo + 1; q < hi; ++q) {
-                const T vq = f[SK::f(q)];
-                while (s0 >= 0 && hidden_v(s0, v0, s1, v1, q, vq, hh)) {
+            T* fl = f + SK::f(lo);
+            short* sl = stk + SK::s(lo);
+            const int cnt = hi - lo;
+            int top = 0;
+            bool has0 = false;
+            T s1 = (T)lo, v1 = fl[0], s0 = (T)0, v0 = (T)0;
+            T xq = (T)lo;
+            sl[0] = (short)lo;
+            for (int k = 1; k < cnt; ++k) {
+                xq += (T)1;
+                const T vq = fl[k];
+                while (has0 && hidden_t(s0, v0, s1, v1, xq, vq, hh)) {
                     --top;
                     s1 = s0; v1 = v0;
-                    if (top > lo) { s0 = stk[SK::s(top - 1)]; v0 = f[SK::f(top - 1)]; }
-                    else s0 = -1;
+                    if (top > 0) { s0 = (T)sl[top - 1]; v0 = fl[top - 1]; }
+                    else has0 = false;
                 }
                 ++top;
-                stk[SK::s(top)] = (short)q;
-                f[SK::f(top)] = vq;
-                s0 = s1; v0 = v1;
-                s1 = q; v1 = vq;
+                sl[top] = (short)(lo + k);
+                fl[top] = vq;
+                s0 = s1; v0 = v1; has0 = true;
+                s1 = xq; v1 = vq;
             }
             beg[t] = (short)lo;
-            end[t] = (short)(top + 1);
+            end[t] = (short)(lo + top + 1);
         } else {
             beg[t] = 0;
             end[t] = 0;
@@ -570,7 +658,7 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
         group_sync(w, G);
         // ---- B: pairwise merges ----------------------------------------------
         for (int s = 1; s < G; s <<= 1) {
-            if ((t & (2 * s - 1)) == 0 && t + s < G) merge_pair<K>(f, stk, beg, end, t, s, n, hh);
+            if ((t & (2 * s - 1)) == 0 && t + s < G) merge_pair_t<K>(f, stk, beg, end, t, s, n, hh);
             if (4 * s <= 32) __syncwarp();
             else group_sync(w, G);
         }
@@ -593,12 +681,13 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
         // ---- D: evaluate this thread's outputs, store, dual dot ----------------
         if (lo < n) {
             const int M = cnt_all[w];
+            const T xlo = (T)lo;
             int ml = 0, mh = M - 1;
             while (ml < mh) {
                 const int mid = (ml + mh + 1) >> 1;
                 const int pu = beg[nzs[mid]], pv = end[nzs[mid - 1]] - 1;
-                if (parab(hh, lo, (int)stk[SK::s(pu)], f[SK::f(pu)]) <
-                    parab(hh, lo, (int)stk[SK::s(pv)], f[SK::f(pv)])) ml = mid;
+                if (parab_t(hh, xlo, (T)stk[SK::s(pu)], f[SK::f(pu)]) <
+                    parab_t(hh, xlo, (T)stk[SK::s(pv)], f[SK::f(pv)])) ml = mid;
                 else mh = mid - 1;
             }
             const int m = ml;
@@ -606,11 +695,11 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
             int pl = beg[nzs[m]], ph = pe - 1;
             while (pl < ph) {
                 const int mid = (pl + ph + 1) >> 1;
-                if (parab(hh, lo, (int)stk[SK::s(mid)], f[SK::f(mid)]) <
-                    parab(hh, lo, (int)stk[SK::s(mid - 1)], f[SK::f(mid - 1)])) pl = mid;
+                if (parab_t(hh, xlo, (T)stk[SK::s(mid)], f[SK::f(mid)]) <
+                    parab_t(hh, xlo, (T)stk[SK::s(mid - 1)], f[SK::f(mid - 1)])) pl = mid;
                 else ph = mid - 1;
             }
-            int jc = stk[SK::s(pl)];
+            T jc = (T)stk[SK::s(pl)];
             T fc = f[SK::f(pl)];
             // the parabola after the current one on the envelope: the next
             // position of its segment, else the first of the next non-empty
@@ -620,29 +709,30 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
                 mn = m + 1;
                 if (mn < M) { pn = beg[nzs[mn]]; pen = end[nzs[mn]]; } else pn = -1;
             }
-            int jn = -1;
-            T fn = (T)0;
-            if (pn >= 0) { jn = stk[SK::s(pn)]; fn = f[SK::f(pn)]; }
+            bool has_n = pn >= 0;
+            T jn = (T)0, fn = (T)0;
+            if (has_n) { jn = (T)stk[SK::s(pn)]; fn = f[SK::f(pn)]; }
             T* dst = a.out + rb;
             const T* wo = a.w_out ? a.w_out + rb : nullptr;
+            T xf = xlo;
             for (int x0 = lo; x0 < hi; x0 += 4) {
                 T o[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int x = x0 + k;
-                    T vc = parab(hh, x, jc, fc);
-                    while (jn >= 0) {
-                        const T vn = parab(hh, x, jn, fn);
+                    T vc = parab_t(hh, xf, jc, fc);
+                    while (has_n) {
+                        const T vn = parab_t(hh, xf, jn, fn);
                         if (!(vn <= vc)) break;
                         jc = jn; fc = fn; vc = vn;           // advance to pn
                         if (pn + 1 < pen) ++pn;
                         else {
                             ++mn;
-                            if (mn < M) { pn = beg[nzs[mn]]; pen = end[nzs[mn]]; } else pn = -1;
+                            if (mn < M) { pn = beg[nzs[mn]]; pen = end[nzs[mn]]; } else has_n = false;
                         }
-                        if (pn >= 0) { jn = stk[SK::s(pn)]; fn = f[SK::f(pn)]; } else jn = -1;
+                        if (has_n) { jn = (T)stk[SK::s(pn)]; fn = f[SK::f(pn)]; }
                     }
                     o[k] = vc;
+                    xf += (T)1;
                 }
                 if (sizeof(T) == 4 && a.vec4 && x0 + 4 <= hi) {
                     float4 v4 = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
