@@ -38,6 +38,8 @@ struct DctArgs {
     double* part;             // MID: per-CTA partial sums of G
     const int* done;          // optional skip flag
     const cx_t<T>* tw;        // e^{-2 pi i j/n}
+    const float2* ptw;        // register FFT: pass twiddles, pass of stride Ns at
+                              // Ns - 1, entry (r - 1) Ns + k = e^{-2 pi i k r/(Ns R)}
     const cx_t<T>* dtw;       // e^{-i pi k/(2n)}
     const unsigned short* drev;   // digit reversal of the stage radices
     const T* lam_axis;        // MID: eigenvalues along this axis
@@ -415,38 +417,42 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[16])
     }
 }
 
+// Twiddles of a pass of stride Ns come from its own block of the pass table,
+// laid out [r][k], so the lanes of a warp (consecutive k) read consecutive
+// entries; the first pass (Ns = 1) has none.
 template <int R, int SIGN, int Bi>
 __device__ __forceinline__ void read_bfly(const float2* z, int n, int Ns, int t, int T,
-                                          const float2* tw, float2 (&v)[16])
+                                          const float2* ptw, float2 (&v)[16])
 {
-    const int step = n / (Ns * R);
     const int j = t + Bi * T;
     const int k = j & (Ns - 1);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[Bi * R + r] = z[padix(j + r * (n / R))];
+    if (Ns > 1) {
+        const float2* pw = ptw + (Ns - 1) + k;
 #pragma unroll
-    for (int r = 1; r < R; ++r) v[Bi * R + r] = cmul_sgn<SIGN>(v[Bi * R + r], tw[(k * r) * step]);
+        for (int r = 1; r < R; ++r) v[Bi * R + r] = cmul_sgn<SIGN>(v[Bi * R + r], pw[(r - 1) * Ns]);
+    }
     dft_reg<R, SIGN, Bi * R>(v);
 }
 
 template <int R, int SIGN>
 __device__ __forceinline__ void pass_read(const float2* z, int n, int Ns, int t, int T,
-                                          const float2* tw, float2 (&v)[16])
+                                          const float2* ptw, float2 (&v)[16])
 {
-    read_bfly<R, SIGN, 0>(z, n, Ns, t, T, tw, v);
-    if (16 / R > 1) read_bfly<R, SIGN, (16 / R > 1 ? 1 : 0)>(z, n, Ns, t, T, tw, v);
+    read_bfly<R, SIGN, 0>(z, n, Ns, t, T, ptw, v);
+    if (16 / R > 1) read_bfly<R, SIGN, (16 / R > 1 ? 1 : 0)>(z, n, Ns, t, T, ptw, v);
     if (16 / R > 2) {
-        read_bfly<R, SIGN, (16 / R > 2 ? 2 : 0)>(z, n, Ns, t, T, tw, v);
-        read_bfly<R, SIGN, (16 / R > 2 ? 3 : 0)>(z, n, Ns, t, T, tw, v);
+        read_bfly<R, SIGN, (16 / R > 2 ? 2 : 0)>(z, n, Ns, t, T, ptw, v);
+        read_bfly<R, SIGN, (16 / R > 2 ? 3 : 0)>(z, n, Ns, t, T, ptw, v);
     }
     if (16 / R > 4) {
 #pragma unroll
         for (int b = 4; b < 8; ++b) {
-            const int step = n / (Ns * R);
             const int j = t + b * T;
             const int k = j & (Ns - 1);
             float2 x0 = z[padix(j)], x1 = z[padix(j + n / R)];
-            x1 = cmul_sgn<SIGN>(x1, tw[k * step]);
+            if (Ns > 1) x1 = cmul_sgn<SIGN>(x1, ptw[(Ns - 1) + k]);
             v[2 * b] = cadd(x0, x1);
             v[2 * b + 1] = csub(x0, x1);
         }
@@ -469,7 +475,7 @@ __device__ __forceinline__ void pass_write(float2* z, int Ns, int t, int T, cons
 
 // One FFT of every pair held by the CTA (all threads take part: barriers).
 template <int SIGN>
-__device__ void stockham_fft(float2* z, int n, int t, int T, bool active, const float2* tw,
+__device__ void stockham_fft(float2* z, int n, int t, int T, bool active, const float2* ptw,
                              int nst, const int* rad)
 {
     float2 v[16];
@@ -477,10 +483,10 @@ __device__ void stockham_fft(float2* z, int n, int t, int T, bool active, const 
     for (int s = 0; s < nst; ++s) {
         const int R = rad[s];
         if (active) {
-            if (R == 16) pass_read<16, SIGN>(z, n, Ns, t, T, tw, v);
-            else if (R == 8) pass_read<8, SIGN>(z, n, Ns, t, T, tw, v);
-            else if (R == 4) pass_read<4, SIGN>(z, n, Ns, t, T, tw, v);
-            else pass_read<2, SIGN>(z, n, Ns, t, T, tw, v);
+            if (R == 16) pass_read<16, SIGN>(z, n, Ns, t, T, ptw, v);
+            else if (R == 8) pass_read<8, SIGN>(z, n, Ns, t, T, ptw, v);
+            else if (R == 4) pass_read<4, SIGN>(z, n, Ns, t, T, ptw, v);
+            else pass_read<2, SIGN>(z, n, Ns, t, T, ptw, v);
         }
         __syncthreads();
         if (active) {
@@ -567,7 +573,7 @@ __global__ void __launch_bounds__(512, 1) dct_fast_kernel(DctArgs<float> a0, con
         }
         __syncthreads();
         if (MODE != DCT_INV) {
-            stockham_fft<-1>(z, n, t, G, active, a.tw, a.fnst, a.frad);
+            stockham_fft<-1>(z, n, t, G, active, a.ptw, a.fnst, a.frad);
             if (active) {
                 for (int k = t; k <= n / 2; k += G) {
                     const int km = (n - k) % n;
@@ -642,7 +648,7 @@ __global__ void __launch_bounds__(512, 1) dct_fast_kernel(DctArgs<float> a0, con
                 }
             }
             __syncthreads();
-            stockham_fft<+1>(z, n, t, G, active, a.tw, a.fnst, a.frad);
+            stockham_fft<+1>(z, n, t, G, active, a.ptw, a.fnst, a.frad);
         }
         // ---- store (the potential update reads its U values first) ------------------
         {
@@ -747,10 +753,21 @@ bool fft_radices(int n, FftRadices* rs)
     return true;
 }
 
+static bool fast_radices(int n, int* nst, int* rad);
+
+// FP32 power-of-two lines from 32 cells run the register FFT and carry its
+// pass twiddle table
+static bool has_pass_table(int n, int elem_bytes)
+{
+    int nst, rad[8];
+    return elem_bytes == 4 && fast_radices(n, &nst, rad);
+}
+
 size_t axis_table_bytes(int n, int elem_bytes)
 {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    return up((size_t)n * 2 * elem_bytes) * 2 + up((size_t)n * 2) + up((size_t)n * 8);
+    return up((size_t)n * 2 * elem_bytes) * 2 + up((size_t)n * 2) + up((size_t)n * 8) +
+           (has_pass_table(n, elem_bytes) ? up((size_t)n * 8) : 0);
 }
 
 bool layout_axis_tables(int n, int elem_bytes, unsigned char* ws, AxisTables* t)
@@ -765,7 +782,33 @@ bool layout_axis_tables(int n, int elem_bytes, unsigned char* ws, AxisTables* t)
     t->dtw = ws + cb;
     t->drev = reinterpret_cast<unsigned short*>(ws + 2 * cb);
     t->lam = ws + 2 * cb + up((size_t)n * 2);
+    t->ptw = has_pass_table(n, elem_bytes) ? ws + 2 * cb + up((size_t)n * 2) + up((size_t)n * 8)
+                                           : nullptr;
     return true;
+}
+
+// Pass twiddles of the register FFT: the pass of radix R and stride Ns (the
+// product of the earlier radices) takes e^{-2 pi i k r/(Ns R)} for k < Ns,
+// 0 < r < R; its block starts at Ns - 1 (the blocks before it hold
+// sum (R' - 1) Ns' = Ns - 1 entries), so all passes fill n - 1 entries.
+struct PassRadices { int nst; int rad[8]; };
+
+__global__ void fill_pass_table_kernel(int n, float2* ptw, PassRadices pr)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n - 1) return;
+    int Ns = 1, R = pr.rad[0];
+    for (int s = 0; s < pr.nst; ++s) {
+        R = pr.rad[s];
+        if (j < Ns * R - 1) break;                 // j in [Ns - 1, Ns R - 1)
+        Ns *= R;
+    }
+    const int local = j - (Ns - 1);
+    const int r = local / Ns + 1, k = local % Ns;
+    double s, c;
+    sincospi(-2.0 * (double)k * (double)r / ((double)Ns * (double)R), &s, &c);
+    ptw[j].x = (float)c;
+    ptw[j].y = (float)s;
 }
 
 template <typename T>
@@ -776,6 +819,12 @@ bfm_status fill_axis_tables(int n, AxisTables* t, unsigned char* ws, cudaStream_
         n, reinterpret_cast<cx_t<T>*>(t->tw), reinterpret_cast<cx_t<T>*>(t->dtw), t->drev,
         reinterpret_cast<T*>(t->lam), t->rs.nst, t->rs);
     BFM_LAUNCH_CHECK("fill_tables_kernel");
+    if (t->ptw) {
+        PassRadices pr;
+        fast_radices(n, &pr.nst, pr.rad);
+        fill_pass_table_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, reinterpret_cast<float2*>(t->ptw), pr);
+        BFM_LAUNCH_CHECK("fill_pass_table_kernel");
+    }
     return BFM_OK;
 }
 
@@ -863,6 +912,11 @@ static bfm_status make_dct_args(const Grid& g, int axis, const DctPlan& p, const
     a->in = in; a->base = base; a->out = out; a->upd = upd; a->sigma = sigma; a->part = part;
     a->done = done;
     a->tw = reinterpret_cast<const cx_t<T>*>(tb.tw);
+    a->ptw = reinterpret_cast<const float2*>(tb.ptw);
+    if (p.fast && !tb.ptw) {
+        set_last_error("internal: DCT pass twiddle table missing");
+        return BFM_ERR_INVALID_ARG;
+    }
     a->dtw = reinterpret_cast<const cx_t<T>*>(tb.dtw);
     a->drev = tb.drev;
     a->lam_axis = reinterpret_cast<const T*>(tb.lam);

@@ -24,6 +24,8 @@ struct AxisTables {
     void* dtw;                // complex, n
     unsigned short* drev;     // n
     void* lam;                // n, element type of the call
+    void* ptw;                // FP32 power-of-two lines: per-pass twiddles of the
+                              // register FFT (n - 1 complex floats), else NULL
 };
 
 struct DctPlan {
