@@ -51,6 +51,32 @@ BYTES_PER_CELL_2D = {
 # an iteration 4 read a weight as well (8 x 8 + 4 x 12 bytes).
 BYTES_PER_CELL_2D_TRANSPOSED = dict(BYTES_PER_CELL_2D, ct_pass_axis1=8,
                                     transpose=(8 * 8 + 4 * 12) / 12)
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# of the launches of that kind in one cold-cache ncu capture, summarised in
+# profiles/ct_row_kernel_annulus5g_4096_fp32.md); reported only while the
+# kernel source still matches the one the counters were taken on
+TRAFFIC = {
+    "ct_pass_axis1": {"bytes": (67147008 + 11566336 + 67147264 + 11705600) / 2,
+                      "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
+                      "sha256": "092ad64594c377510c5f94a6ae977bde7d9a0bd00763938042b38fd9a6fa979b"},
+    "ct_pass_axis0": {"bytes": (134484480 + 25602560 + 135684096 + 27793920) / 2,
+                      "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
+                      "sha256": "092ad64594c377510c5f94a6ae977bde7d9a0bd00763938042b38fd9a6fa979b"},
+}
+
+
+def traffic_of(kind: str):
+    import hashlib
+    t = TRAFFIC.get(kind)
+    if not t:
+        return None
+    try:
+        h = hashlib.sha256(open(os.path.join(ROOT, t["source"]), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return t["bytes"] if h == t["sha256"] else None
+
+
 # the method's own traffic per iteration (4 c-transforms of two sweeps, 2
 # Poisson solves of three sweeps, 2 pushforwards); transposes are not part of it
 METHOD_BYTES_PER_CELL_ITER = 4 * (12 + 12) + 2 * (12 + 8 + 12) + 2 * 16
@@ -296,7 +322,7 @@ def main():
     bytes_per_launch = table[dom] * N
     achieved = bytes_per_launch / (ms / cnt / 1e3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic_of(dom),
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
             "bytes_per_launch": bytes_per_launch, "avg_launch_ms": ms / cnt}
     alg_iter = METHOD_BYTES_PER_CELL_ITER * N
@@ -338,8 +364,10 @@ def main():
             "fp64": {"seconds": t64, "iters": r64["iters"], "converged": r64["converged"],
                      "w2sq": r64["w2sq"], "final_resid": float(r64["resid"][-1])},
             "fp32_vs_fp64": {"rel_dw2sq": abs(r32["w2sq"] - r64["w2sq"]) / r64["w2sq"],
-                             "map_linf_cells": float(torch.max(torch.abs(
-                                 r32["map"].double() - r64["map"])).item() * args.n)},
+                             # where mu > 0: elsewhere the map carries no mass
+                             "map_linf_cells_on_mu_support": float(torch.max(torch.abs(
+                                 r32["map"].double() - r64["map"]).reshape(2, -1)[:, mu.reshape(-1) > 0]
+                             ).item() * args.n)},
         }
         # plain FP64 iterations/s on the same GPU
         s64 = B.BfmSolver(torch.from_numpy(mu_h).to(dev), torch.from_numpy(nu_h).to(dev),

@@ -334,6 +334,10 @@ static bfm_status poisson_inverse(const Grid& g, const AxisTables* tabs, T* buf,
     return BFM_OK;
 }
 
+// one CTA sums the FP64 partials of a half step's reductions (up to a few
+// thousand: one per CTA of the launch that produced them)
+constexpr int kFinThreads = 1024;
+
 template <typename T>
 bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
                             Logs logs, cudaStream_t st)
@@ -358,7 +362,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
-        finalize_dual_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+        finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
                                                 phi_half ? 0 : 2, logs);
         BFM_LAUNCH_CHECK("finalize_dual_kernel");
     }
@@ -371,7 +375,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
-        finalize_G_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 2), ng, phi_half ? 0 : 1, logs);
+        finalize_G_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 2), ng, phi_half ? 0 : 1, logs);
         BFM_LAUNCH_CHECK("finalize_G_kernel");
     }
     s = poisson_inverse<T>(g, w->tabs, rho, src, src, &w->state->sigma, done, st);
@@ -380,7 +384,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
-        finalize_dual_kernel<<<1, 256, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+        finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
                                                 phi_half ? 1 : 3, logs);
         BFM_LAUNCH_CHECK("finalize_dual_kernel");
     }
