@@ -511,8 +511,9 @@ __device__ void merge_pair_t(const T* f, const short* stk, short* beg, short* en
 }
 
 // ---------------------------------------------------------------------------
-// Row sweeps of long lines (axis 0, n >= kRowMinN): one group of G threads
-// per line, K = 32 cells per thread.  Compared with the tile kernel above:
+// Row sweeps of long lines (axis 0, n > kRowMinN): one group of G threads
+// per line, K = 32 cells per thread from 1024 cells, else 16 (G >= 32 either
+// way).  Compared with the tile kernel above:
 //   * lines are independent: each group takes rows g, g + groups, ... and
 //     synchronises only its own G threads, so no line waits for another;
 //   * shared memory holds only the line values (the stacks in place) and the
@@ -526,8 +527,10 @@ __device__ void merge_pair_t(const T* f, const short* stk, short* beg, short* en
 //     time (a thread's 32 outputs are one 128-byte line), fused with the dual
 //     dot product.
 // ---------------------------------------------------------------------------
-constexpr int kRowK = 32;
-constexpr int kRowMinN = 1024;
+constexpr int kRowMinN = 256;          // rows longer than this take the row kernel
+constexpr int kRowLongN = 1024;        // from here 32 cells per thread, else 16
+
+static int row_cells_per_thread(int n) { return n >= kRowLongN ? 32 : 16; }
 
 // Barrier of one line group (G >= 32 threads, whole warps): a single warp
 // uses the warp barrier, larger groups named barrier 1 + w.
@@ -875,16 +878,16 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
     return p;
 }
 
-static bool use_row_kernel(const Grid& g, int axis) { return axis == 0 && g.n[0] >= kRowMinN; }
+static bool use_row_kernel(const Grid& g, int axis) { return axis == 0 && g.n[0] > kRowMinN; }
 
-// Row kernel plan: K = 32 cells per thread, G = the next power of two of
-// n / 32 (at least 32, so every group is whole warps), as many groups per
-// CTA as fit 512 threads and about 110 KB (two CTAs per SM).
+// Row kernel plan: K = 32 or 16 cells per thread, G = the next power of two
+// of n / K (at least 32 for n > 256, so every group is whole warps), as many
+// groups per CTA as fit 512 threads and about 110 KB (two CTAs per SM).
 static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
 {
     CtPlan p;
     const int n = g.n[0];
-    p.K = kRowK;
+    p.K = row_cells_per_thread(n);
     p.G = next_pow2((n + p.K - 1) / p.K);
     const int chunks = (n + p.K - 1) / p.K + 1;
     p.LD = n + chunks + 2;
@@ -947,7 +950,7 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
         CtPlan p = plan_ct_row(g, (int)sizeof(T));
         CtArgs<T> a = make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out,
                                       done);
-        void* k = (void*)ct_row_kernel<T, kRowK>;
+        void* k = (p.K == 32) ? (void*)ct_row_kernel<T, 32> : (void*)ct_row_kernel<T, 16>;
         BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
         long long blocks = (p.tiles.nlines + p.W - 1) / p.W;
         const long long cap = (long long)num_sms() * 2;      // two resident CTAs per SM

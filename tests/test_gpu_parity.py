@@ -40,10 +40,11 @@ def host(t):
     return t.detach().double().cpu().numpy()
 
 
-# rows of 1024 cells or more take the row kernel (32 cells per thread, one
-# thread group per row): aligned, ragged (1500) and unaligned (1027) lengths
+# rows of more than 256 cells take the row kernel (one thread group per row,
+# 16 cells per thread below 1024, else 32): aligned, ragged (257, 300, 1500)
+# and unaligned (511, 1027) lengths, in 2-D and 3-D
 CT_SHAPES = [(2, 2), (7, 5), (64, 64), (33, 100), (257, 96), (48, 31, 20), (9, 40, 13),
-             (1024, 3), (1500, 4), (1027, 3), (4096, 2)]
+             (300, 5, 3), (511, 7), (1024, 3), (1500, 4), (1027, 3), (4096, 2)]
 
 
 @pytest.mark.parametrize("shape", CT_SHAPES, ids=str)
