@@ -190,6 +190,38 @@ def workload_config(n):
             "l2": "inputs larger than L2 (6 resident fields of 64 MiB each)", "tol": 1e-3}
 
 
+def paper_comparison(B, dev, stream) -> dict:
+    """Section 5, Tables 5-6 on this GPU: the back-and-forth method against
+    the H1-dot gradient ascent on J, two discs and one square to four squares
+    at 1024^2, FP64; iterations until |J - exact cost| < 1e-4, 1e-5, 1e-6 and
+    the time to get there (the run's wall time per iteration, setup included,
+    times those iterations)."""
+    import numpy as np
+    import torch
+    import synthetic_inputs as si
+    out = {}
+    for name, pair, exact in (("two_discs", si.translated_discs, 0.25),
+                              ("square_to_four_squares", si.square_to_four, 0.0625)):
+        mu, nu = (torch.from_numpy(x).to(dev) for x in pair(1024))
+        row = {}
+        for method, cap in (("bfm", 40), ("ga", 1500)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = B.bfm_solve(mu, nu, tol=0.0, max_iter=cap, with_map=False, method=method)
+            t = time.perf_counter() - t0
+            err = np.abs(r["dual"] - exact)
+            per_it = t / max(r["iters"], 1)
+            row[method] = {e: ({"iterations": int(np.argmax(err < float(e))),
+                                "seconds": round(int(np.argmax(err < float(e))) * per_it, 4)}
+                               if np.any(err < float(e)) else None)
+                           for e in ("1e-4", "1e-5", "1e-6")}
+            row[method]["ms_per_iteration"] = round(per_it * 1e3, 3)
+        out[name] = row
+    out["grid"] = [1024, 1024]
+    out["precision"] = "FP64"
+    return out
+
+
 def other_workloads(B, dev, stream, args) -> dict:
     """The 384^3 3D solve, 128 batched uneven problems and the 32-pair loss."""
     import numpy as np
@@ -397,6 +429,7 @@ def main():
         # ---- the other workloads: 3D, batched uneven solves, the W2^2 loss ---------------
         if not args.no_workloads:
             line["workloads"] = other_workloads(B, dev, stream, args)
+            line["bfm_vs_gradient_ascent"] = paper_comparison(B, dev, stream)
         # ---- the FP64 CPU oracle on the host cores ----------------------------------------
         if ws == 1 and not args.no_cpu_baseline:
             import oracle

@@ -66,16 +66,26 @@ typedef struct {
     int n[3];       /* cells per axis; n[2] ignored when ndim == 2 */
 } bfm_grid;
 
+/* The iteration.  BFM_BACK_AND_FORTH is Algorithm 1 (the default).
+ * BFM_GRADIENT_ASCENT is the plain H1-dot gradient ascent on J that Section 5
+ * compares it with (Tables 5 and 6): phi_{n+1/2} = phi_n + sigma grad J(phi_n),
+ * phi_{n+1} = (phi_{n+1/2})^{cc}; two c-transforms and one Poisson solve per
+ * iteration (phi_{n+1}^c = (phi_{n+1/2})^c is kept for the next gradient), the
+ * step rule of Section 4.2 applied to J(phi_{n+1/2}) - J(phi_n), and the
+ * residual, logs and outputs of Algorithm 1 (dual[n] = J(phi_n)). */
+typedef enum { BFM_BACK_AND_FORTH = 0, BFM_GRADIENT_ASCENT = 1 } bfm_method;
+
 /* Step-size rule of Section 4.2 and loop control.  bfm_default_options()
  * fills the paper's values: beta1 = 1/4, beta2 = 3/4, alpha1 = 5/4,
  * alpha2 = 4/5, sigma0 <= 0 meaning 8 min(1/|mu|_inf, 1/|nu|_inf),
- * sigma_min = 0.01. */
+ * sigma_min = 0.01, and method = BFM_BACK_AND_FORTH. */
 typedef struct {
     double beta1, beta2, alpha1, alpha2;
     double sigma0;
     double sigma_min;
     int poll_every;          /* host reads the device convergence flag every k iterations (default 4) */
     int warm_start;          /* nonzero: result->phi holds the initial phi on entry (else phi_0 = 0) */
+    int method;              /* bfm_method */
 } bfm_options;
 
 typedef struct {
@@ -140,10 +150,12 @@ bfm_status bfm_solve(const void *mu, const void *nu, const bfm_grid *grid, bfm_c
  *                       phi_0 = 0 (or keeps phi when opt->warm_start) in `phi`;
  *                       `phi`, `psi` are DEVICE fields of N elements that hold
  *                       the iterates.  Synchronises once to check the inputs.
- *   bfm_solver_iterate  enqueues `iterations` back-and-forth iterations on
- *                       `stream` without synchronising; once the device has
- *                       converged (or reached max_iter) further iterations do
- *                       no work.
+ *   bfm_solver_iterate  enqueues `iterations` iterations of opt->method (opt:
+ *                       the options given to bfm_solver_init, NULL for the
+ *                       defaults) on `stream` without synchronising; once the
+ *                       device has converged (or reached max_iter) further
+ *                       iterations do no work.  With BFM_GRADIENT_ASCENT the
+ *                       `psi` field is written by bfm_solver_finish only.
  *   bfm_solver_finish   measures the current phi_n if the loop has not
  *                       stopped, then fills `out` exactly as bfm_solve does
  *                       (out->phi and out->psi must be the `phi`, `psi` of the
@@ -154,8 +166,8 @@ bfm_status bfm_solver_init(const void *mu, const void *nu, const bfm_grid *grid,
                            void *workspace, size_t workspace_bytes, void *stream,
                            void *phi, void *psi);
 bfm_status bfm_solver_iterate(const bfm_grid *grid, bfm_precision prec, int max_iter,
-                              int iterations, void *workspace, size_t workspace_bytes,
-                              void *stream, void *phi, void *psi);
+                              int iterations, const bfm_options *opt, void *workspace,
+                              size_t workspace_bytes, void *stream, void *phi, void *psi);
 bfm_status bfm_solver_finish(const bfm_grid *grid, bfm_precision prec, int max_iter,
                              void *workspace, size_t workspace_bytes, void *stream,
                              bfm_result *out);

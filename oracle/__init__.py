@@ -191,8 +191,10 @@ DEFAULTS = dict(beta1=0.25, beta2=0.75, alpha1=1.25, alpha2=0.8, sigma0=0.0,
 
 
 def solve(mu, nu, tol: float = 1e-6, max_iter: int = 300, ct_mode: str = "linear",
-          dct_mode: str = "fft", **opts) -> dict:
-    """Algorithm 1 with the step rule of Section 4.2, in FP64.
+          dct_mode: str = "fft", method: str = "bfm", **opts) -> dict:
+    """Algorithm 1 with the step rule of Section 4.2, in FP64 (method "bfm"),
+    or the H1-dot gradient ascent on J it is compared with in Section 5
+    (method "ga": phi += sigma grad J(phi), then phi = phi^cc).
 
     Returns phi, psi (= phi^c), map (d, *grid), w2sq (= 2 J(phi)), iters,
     converged, dual / resid / sigma logs (length iters+1) and the half-step
@@ -203,7 +205,8 @@ def solve(mu, nu, tol: float = 1e-6, max_iter: int = 300, ct_mode: str = "linear
     o.update(opts)
     optv = np.array([o["beta1"], o["beta2"], o["alpha1"], o["alpha2"], o["sigma0"],
                      o["sigma_min"], {"brute": 0, "linear": 1}[ct_mode],
-                     {"definition": 0, "fft": 1}[dct_mode]], dtype=np.float64)
+                     {"definition": 0, "fft": 1}[dct_mode],
+                     {"bfm": 0, "ga": 1}[method]], dtype=np.float64)
     nd, n = _grid(mu.shape)
     phi = np.empty_like(mu)
     psi = np.empty_like(mu)

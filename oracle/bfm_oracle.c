@@ -494,6 +494,7 @@ typedef struct {
     double sigma_min;                     /* 0.01 */
     int ct_mode;                          /* 0 brute, 1 Legendre/linear */
     int dct_mode;                         /* 0 definition, 1 FFT */
+    int method;                           /* 0 back-and-forth, 1 gradient ascent on J */
 } oracle_opts;
 
 typedef struct {
@@ -556,11 +557,11 @@ int bfm_oracle_solve(const double *mu_in, const double *nu_in, int ndim, const i
 {
     grid_t g;
     if (make_grid(ndim, n, &g)) return -1;
-    oracle_opts o = {0.25, 0.75, 1.25, 0.8, 0.0, 0.01, 1, 1};
+    oracle_opts o = {0.25, 0.75, 1.25, 0.8, 0.0, 0.01, 1, 1, 0};
     if (opt_in) {
         o.beta1 = opt_in[0]; o.beta2 = opt_in[1]; o.alpha1 = opt_in[2]; o.alpha2 = opt_in[3];
         o.sigma0 = opt_in[4]; o.sigma_min = opt_in[5];
-        o.ct_mode = (int)opt_in[6]; o.dct_mode = (int)opt_in[7];
+        o.ct_mode = (int)opt_in[6]; o.dct_mode = (int)opt_in[7]; o.method = (int)opt_in[8];
     }
     long N = g.N;
     double *mu = malloc(sizeof(double) * N), *nu = malloc(sizeof(double) * N);
@@ -582,7 +583,34 @@ int bfm_oracle_solve(const double *mu_in, const double *nu_in, int ndim, const i
     bfm_oracle_poisson(f, gr, ndim, n, o.dct_mode, &Gref);
     int it = 0, conv = 0;
     double Jold = 0.0;
-    for (it = 0; it <= max_iter; it++) {
+    /*
+     * The comparison method of Section 5 (Tables 5 and 6): H1-dot gradient
+     * ascent on J alone, phi_{n+1/2} = phi_n + sigma grad J(phi_n),
+     * phi_{n+1} = (phi_{n+1/2})^{cc}.  Reading: the step rule of Section 4.2
+     * compares J(phi_{n+1/2}) with J(phi_n); residual, logs and outputs as for
+     * Algorithm 1 (half[3n] = J(phi_{n+1/2})).
+     */
+    if (o.method == 1) for (it = 0; it <= max_iter; it++) {
+        bfm_oracle_ctransform(phi, tmp, ndim, n, o.ct_mode);          /* phi_n^c */
+        Jold = dot_hd(&g, phi, nu) + dot_hd(&g, tmp, mu);
+        bfm_oracle_pushforward(tmp, mu, rho, ndim, n);
+        for (long i = 0; i < N; i++) f[i] = nu[i] - rho[i];
+        double G;
+        bfm_oracle_poisson(f, gr, ndim, n, o.dct_mode, &G);
+        double r = (Gref > 0) ? sqrt(fmax(G, 0.0) / Gref) : sqrt(fmax(G, 0.0));
+        if (dual) dual[it] = Jold;
+        if (resid) resid[it] = r;
+        if (sig) sig[it] = sigma;
+        if (r < tol) { conv = 1; break; }
+        if (it == max_iter) break;
+        for (long i = 0; i < N; i++) phi[i] += sigma * gr[i];        /* phi_{n+1/2} */
+        bfm_oracle_ctransform(phi, psi, ndim, n, o.ct_mode);          /* phi_{n+1/2}^c */
+        double Jnew = dot_hd(&g, phi, nu) + dot_hd(&g, psi, mu);
+        sigma = step_rule(sigma, Jnew - Jold, G, &o);
+        bfm_oracle_ctransform(psi, phi, ndim, n, o.ct_mode);          /* phi_{n+1} */
+        if (half) { half[3 * it + 0] = Jnew; half[3 * it + 1] = 0.0; half[3 * it + 2] = 0.0; }
+    }
+    if (o.method == 0) for (it = 0; it <= max_iter; it++) {
         /* phi-half step */
         bfm_oracle_ctransform(phi, tmp, ndim, n, o.ct_mode);          /* psi~ = phi^c */
         Jold = dot_hd(&g, phi, nu) + dot_hd(&g, tmp, mu);

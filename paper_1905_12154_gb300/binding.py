@@ -28,6 +28,8 @@ BFM_ERR_UNSUPPORTED = -5
 BFM_ERR_WORKSPACE = -6
 BFM_FP32 = 0
 BFM_FP64 = 1
+BFM_BACK_AND_FORTH = 0
+BFM_GRADIENT_ASCENT = 1
 BFM_COST_QUADRATIC = 0
 
 
@@ -39,7 +41,8 @@ class bfm_options(ctypes.Structure):
     _fields_ = [("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double),
                 ("sigma0", ctypes.c_double), ("sigma_min", ctypes.c_double),
-                ("poll_every", ctypes.c_int), ("warm_start", ctypes.c_int)]
+                ("poll_every", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("method", ctypes.c_int)]
 
 
 class bfm_result(ctypes.Structure):
@@ -88,8 +91,9 @@ _SIGS = {
     "bfm_solver_init": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_int, ctypes.POINTER(bfm_options), _P,
                                        ctypes.c_size_t, _P, _P, _P]),
-    "bfm_solver_iterate": (ctypes.c_int, [_GP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
-                                          ctypes.c_size_t, _P, _P, _P]),
+    "bfm_solver_iterate": (ctypes.c_int, [_GP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(bfm_options), _P, ctypes.c_size_t, _P,
+                                          _P, _P]),
     "bfm_solver_finish": (ctypes.c_int, [_GP, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t,
                                          _P, ctypes.POINTER(bfm_result)]),
     "bfm_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.c_int, _GP, ctypes.c_int,
@@ -198,11 +202,19 @@ def _user_workspace(buf):
     return buf, buf.data_ptr() + off, max(0, buf.numel() * buf.element_size() - off)
 
 
+METHODS = {"bfm": BFM_BACK_AND_FORTH, "back_and_forth": BFM_BACK_AND_FORTH,
+           "ga": BFM_GRADIENT_ASCENT, "gradient_ascent": BFM_GRADIENT_ASCENT}
+
+
 def _options(**kw) -> bfm_options:
+    """bfm_options with the paper's defaults, overridden by keyword (method may
+    be given as "bfm" / "ga")."""
     o = bfm_options()
     lib().bfm_default_options(ctypes.byref(o))
     for k, v in kw.items():
         if v is not None:
+            if k == "method" and isinstance(v, str):
+                v = METHODS[v]
             setattr(o, k, v)
     return o
 
@@ -395,17 +407,18 @@ class BfmSolver:
             opts["warm_start"] = 1
         self.nbytes = lib().bfm_workspace_bytes(ctypes.byref(self.grid), self.prec, self.max_iter)
         self._ws_keep, self._ws = _workspace(self.nbytes, mu.device)
-        o = _options(**opts)
+        self._opts = _options(**opts)
         _check(lib().bfm_solver_init(mu.data_ptr(), nu.data_ptr(), ctypes.byref(self.grid),
                                      BFM_COST_QUADRATIC, self.prec, float(tol), self.max_iter,
-                                     ctypes.byref(o), self._ws, self.nbytes, _stream(),
+                                     ctypes.byref(self._opts), self._ws, self.nbytes, _stream(),
                                      self.phi.data_ptr(), self.psi.data_ptr()),
                "bfm_solver_init")
 
     def iterate(self, k: int = 1):
         _check(lib().bfm_solver_iterate(ctypes.byref(self.grid), self.prec, self.max_iter, int(k),
-                                        self._ws, self.nbytes, _stream(), self.phi.data_ptr(),
-                                        self.psi.data_ptr()), "bfm_solver_iterate")
+                                        ctypes.byref(self._opts), self._ws, self.nbytes, _stream(),
+                                        self.phi.data_ptr(), self.psi.data_ptr()),
+               "bfm_solver_iterate")
 
     def finish(self, with_map: bool = True) -> dict:
         import torch

@@ -473,6 +473,10 @@ extern "C" bfm_status bfm_solve_batched(int nprob, const void* const* mu, const 
     bfm_default_options(&o);
     if (opt) o = *opt;
     if (o.warm_start) { set_last_error("warm start is not supported in batched solves"); return BFM_ERR_UNSUPPORTED; }
+    if (o.method != BFM_BACK_AND_FORTH) {
+        set_last_error("batched solves run the back-and-forth iteration only");
+        return BFM_ERR_UNSUPPORTED;
+    }
     if (!(o.beta1 > 0 && o.beta1 < o.beta2 && o.beta2 < 1 && o.alpha1 > 1 && o.alpha2 > 0 &&
           o.alpha2 < 1 && o.sigma_min >= 0))
         return BFM_ERR_INVALID_ARG;

@@ -107,4 +107,5 @@ extern "C" void bfm_default_options(bfm_options* o)
     o->sigma_min = 0.01;
     o->poll_every = 4;
     o->warm_start = 0;
+    o->method = BFM_BACK_AND_FORTH;
 }

@@ -391,6 +391,57 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     return BFM_OK;
 }
 
+// One iteration of the H1-dot gradient ascent on J compared with the method in
+// Section 5: on entry tmp holds psi_n = phi_n^c and J(phi_n) is logged;
+//   rho = (x - grad psi_n) # mu, g = (-Delta)^{-1}(nu - rho) (residual, stop),
+//   phi_{n+1/2} = phi_n + sigma g, psi_{n+1} = phi_{n+1/2}^c (step rule on
+//   J(phi_{n+1/2}) - J(phi_n)), phi_{n+1} = psi_{n+1}^c, J(phi_{n+1}) =
+//   <phi_{n+1}, nu> + <psi_{n+1}, mu> logged (psi_{n+1}^{cc} = psi_{n+1}).
+template <typename T>
+static bfm_status ascent_step(const Grid& g, Workspace* w, T* phi, Logs logs, cudaStream_t st)
+{
+    const double hd = 1.0 / (double)g.N;
+    const int* done = &w->state->done;
+    T* mu = (T*)w->mu_n;
+    T* nu = (T*)w->nu_n;
+    T* tmp = (T*)w->tmp;
+    T* rho = (T*)w->rho;
+    T* xt = (T*)w->xt;
+    int ni = 0, no = 0, ng = 0;
+    bfm_status s;
+    {
+        ProfScope ps(PK_PUSH, 1, st);
+        s = launch_pushforward<T>(g, tmp, mu, rho, done, st);
+        if (s != BFM_OK) return s;
+    }
+    s = poisson_forward<T>(g, w->tabs, rho, nu, rho, slot(w, 2), &ng, done, st, xt);
+    if (s != BFM_OK) return s;
+    {
+        ProfScope ps(PK_SMALL, 1, st);
+        finalize_G_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 2), ng, 0, logs);
+        BFM_LAUNCH_CHECK("finalize_G_kernel");
+    }
+    s = poisson_inverse<T>(g, w->tabs, rho, phi, phi, &w->state->sigma, done, st);
+    if (s != BFM_OK) return s;
+    s = ct_with_dots<T>(g, phi, tmp, nu, mu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
+    if (s != BFM_OK) return s;
+    {
+        ProfScope ps(PK_SMALL, 1, st);
+        finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+                                                        3, logs);
+        BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    }
+    s = ct_with_dots<T>(g, tmp, phi, mu, nu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
+    if (s != BFM_OK) return s;
+    {
+        ProfScope ps(PK_SMALL, 1, st);
+        finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+                                                        0, logs);
+        BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    }
+    return BFM_OK;
+}
+
 template <typename T>
 static bfm_status measure_density(const Grid& g, const T* x, Workspace* w, int which, cudaStream_t st)
 {
@@ -463,17 +514,34 @@ bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int ma
     if (!o.warm_start) BFM_CUDA(cudaMemsetAsync(phi, 0, sizeof(T) * g.N, st));
     BFM_CUDA(cudaMemsetAsync(psi, 0, sizeof(T) * g.N, st));
     BFM_CUDA(cudaMemsetAsync(w.logs, 0, sizeof(double) * 3 * (max_iter + 1), st));
+    if (o.method == BFM_GRADIENT_ASCENT) {
+        // the ascent keeps psi_n = phi_n^c in tmp; measure J(phi_0)
+        int ni = 0, no = 0;
+        s = ct_with_dots<T>(g, phi, (T*)w.tmp, (const T*)w.nu_n, (const T*)w.mu_n, slot(&w, 0), &ni,
+                            slot(&w, 1), &no, &w.state->done, st, (T*)w.xt);
+        if (s != BFM_OK) return s;
+        finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w.state, slot(&w, 0), ni, slot(&w, 1), no,
+                                                        1.0 / (double)g.N, 0, logs);
+        BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    }
     return BFM_OK;
 }
 
 // Enqueue `iters` back-and-forth iterations; no host synchronisation.
 template <typename T>
-static bfm_status iterate_impl(const Grid& g, int max_iter, int iters, unsigned char* wsp,
-                               cudaStream_t st, T* phi, T* psi)
+static bfm_status iterate_impl(const Grid& g, int max_iter, int iters, int method,
+                               unsigned char* wsp, cudaStream_t st, T* phi, T* psi)
 {
     Workspace w;
     carve(g, sizeof(T), max_iter, wsp, &w, true);
     Logs logs = logs_of(&w, max_iter);
+    if (method == BFM_GRADIENT_ASCENT) {
+        for (int c = 0; c < iters; ++c) {
+            bfm_status s = ascent_step<T>(g, &w, phi, logs, st);
+            if (s != BFM_OK) return s;
+        }
+        return BFM_OK;
+    }
     for (int c = 0; c < iters; ++c) {
         bfm_status s = half_step<T>(g, &w, true, phi, psi, logs, st); if (s != BFM_OK) return s;
         s = half_step<T>(g, &w, false, phi, psi, logs, st); if (s != BFM_OK) return s;
@@ -616,6 +684,10 @@ extern "C" bfm_status bfm_solver_init(const void* mu, const void* nu, const bfm_
         set_last_error("step rule needs 0 < beta1 < beta2 < 1, alpha1 > 1, 0 < alpha2 < 1");
         return BFM_ERR_INVALID_ARG;
     }
+    if (o.method != BFM_BACK_AND_FORTH && o.method != BFM_GRADIENT_ASCENT) {
+        set_last_error("unknown method");
+        return BFM_ERR_INVALID_ARG;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* wsp = (unsigned char*)workspace;
     if (prec == BFM_FP32)
@@ -626,18 +698,23 @@ extern "C" bfm_status bfm_solver_init(const void* mu, const void* nu, const bfm_
 }
 
 extern "C" bfm_status bfm_solver_iterate(const bfm_grid* grid, bfm_precision prec, int max_iter,
-                                         int iterations, void* workspace, size_t workspace_bytes,
-                                         void* stream, void* phi, void* psi)
+                                         int iterations, const bfm_options* opt, void* workspace,
+                                         size_t workspace_bytes, void* stream, void* phi, void* psi)
 {
     Grid g;
     bfm_status s = check_solver_args(grid, prec, max_iter, workspace, workspace_bytes, &g);
     if (s != BFM_OK) return s;
     if (!phi || !psi || iterations < 0) return BFM_ERR_INVALID_ARG;
+    const int method = opt ? opt->method : BFM_BACK_AND_FORTH;
+    if (method != BFM_BACK_AND_FORTH && method != BFM_GRADIENT_ASCENT) {
+        set_last_error("unknown method");
+        return BFM_ERR_INVALID_ARG;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* wsp = (unsigned char*)workspace;
     if (prec == BFM_FP32)
-        return iterate_impl<float>(g, max_iter, iterations, wsp, st, (float*)phi, (float*)psi);
-    return iterate_impl<double>(g, max_iter, iterations, wsp, st, (double*)phi, (double*)psi);
+        return iterate_impl<float>(g, max_iter, iterations, method, wsp, st, (float*)phi, (float*)psi);
+    return iterate_impl<double>(g, max_iter, iterations, method, wsp, st, (double*)phi, (double*)psi);
 }
 
 extern "C" bfm_status bfm_solver_finish(const bfm_grid* grid, bfm_precision prec, int max_iter,
@@ -669,7 +746,7 @@ extern "C" bfm_status bfm_solve(const void* mu, const void* nu, const bfm_grid* 
     int enq = 0;
     while (enq <= max_iter) {
         const int chunk = (max_iter + 1 - enq) < poll ? (max_iter + 1 - enq) : poll;
-        s = bfm_solver_iterate(grid, prec, max_iter, chunk, workspace, workspace_bytes, stream,
+        s = bfm_solver_iterate(grid, prec, max_iter, chunk, opt, workspace, workspace_bytes, stream,
                                out->phi, out->psi);
         if (s != BFM_OK) return s;
         enq += chunk;

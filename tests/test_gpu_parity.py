@@ -339,3 +339,48 @@ def test_long_columns_take_transposed_sweeps(B, shape, dt):
     assert prof["ct_pass_axis0"][1] == prof["ct_pass_axis1"][1] == 4
     assert prof["dct_fwd"][1] == prof["dct_mid"][1] == prof["dct_inv"][1] == 2
     assert prof["_dropped"][1] == 0
+
+
+# --- the gradient-ascent baseline of Section 5 (Tables 5-6) -------------------
+
+def test_gradient_ascent_fp64_matches_oracle(B):
+    """phi += sigma grad J(phi), phi = phi^cc: the GPU keeps phi^c from the
+    previous step (2 c-transforms per iteration), the oracle recomputes it;
+    both follow the same iterates to rounding."""
+    mu, nu = si.translated_discs(64)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=30, method="ga")
+    r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=30, method="ga")
+    assert r["iters"] == ref["iters"] == 30
+    assert np.max(np.abs(r["dual"] - ref["dual"])) < 1e-11
+    assert np.max(np.abs(r["resid"] - ref["resid"])) < 1e-8
+    assert np.max(np.abs(r["sigma"] - ref["sigma"])) < 1e-12
+    assert np.max(np.abs(host(r["phi"]) - ref["phi"])) < 1e-9
+    assert np.max(np.abs(host(r["psi"]) - ref["psi"])) < 1e-9
+
+
+def test_gradient_ascent_fp32_and_stepwise(B):
+    mu, nu = si.workload_gauss_disc_64(64)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=25, method="ga")
+    r = B.bfm_solve(dev(mu, torch.float32), dev(nu, torch.float32), tol=0.0, max_iter=25,
+                    method="ga")
+    assert abs(r["w2sq"] - ref["w2sq"]) / ref["w2sq"] < 1e-5
+    s = B.BfmSolver(dev(mu, torch.float32), dev(nu, torch.float32), tol=0.0, max_iter=25,
+                    method="ga")
+    B.bfm_profile_begin(400)
+    s.iterate(3)
+    prof = B.bfm_profile_end()
+    # per iteration: 2 c-transforms (2 sweeps each), 1 pushforward, 1 Poisson solve
+    assert prof["ct_pass_axis0"][1] == prof["ct_pass_axis1"][1] == 6
+    assert prof["pushforward"][1] == 3
+    assert prof["dct_fwd"][1] == prof["dct_mid"][1] == prof["dct_inv"][1] == 3
+    s.iterate(22)
+    rs = s.finish(with_map=False)
+    assert rs["iters"] == r["iters"]
+    # FP32 atomics in the pushforward add in a run-dependent order
+    assert np.max(np.abs(rs["dual"] - r["dual"])) < 1e-7
+
+
+def test_gradient_ascent_rejected_by_batched_solver(B):
+    mu, nu = si.translated_discs(16)
+    with pytest.raises(B.BfmError):
+        B.bfm_solve_batched([dev(mu)], [dev(nu)], tol=0.0, max_iter=3, method="ga")

@@ -210,6 +210,25 @@ def pin_solve_square_to_four():
     assert np.all(r["dual"] <= gold["exact_cost"] + 1e-12)
 
 
+def pin_gradient_ascent_baseline():
+    """Section 5, Tables 5-6: the H1-dot gradient ascent on J alone (phi +=
+    sigma grad J, then phi^cc) reaches the closed-form cost of the two discs
+    (Table 1's 1/4) but needs many more iterations than the back-and-forth
+    method (Table 5: 50 vs 3 to 1e-4).  Its first gradient step is Algorithm
+    1's first phi-half step (same phi_0, same gradient), so J(phi_{1/2})
+    agrees exactly."""
+    gold = GOLDEN["translated_discs_2d"]
+    mu, nu = si.translated_discs(64)
+    ga = oracle.solve(mu, nu, tol=0.0, max_iter=120, method="ga")
+    bf = oracle.solve(mu, nu, tol=0.0, max_iter=10)
+    first = lambda r, e: int(np.argmax(np.abs(r["dual"] - gold["exact_cost"]) < e)) \
+        if np.any(np.abs(r["dual"] - gold["exact_cost"]) < e) else 10 ** 6
+    assert first(ga, 1e-6) < 120                       # converges to the exact cost
+    assert first(ga, 1e-4) >= 4 * first(bf, 1e-4)
+    assert ga["half"][0, 0] == bf["half"][0, 0]
+    assert np.all(ga["dual"] <= gold["exact_cost"] + 1e-12)   # weak duality
+
+
 def pin_solve_chain_invariants():
     """Section 3.2: a c-transform never lowers the dual value, so
     J(phi_{n+1/2}) <= I(psi_{n+1/2}) and I(psi_{n+1}) <= J(phi_{n+1})."""
@@ -309,7 +328,8 @@ FAST_PINS = [
     pin_map_quadratic_and_bilinear_weights, pin_solve_translated_discs,
     pin_solve_chain_invariants, pin_step_rule_constants, pin_interpolate_translation,
 ]
-ALL_PINS = FAST_PINS + [pin_solve_square_to_four, pin_solve_weak_duality_lp,
+ALL_PINS = FAST_PINS + [pin_solve_square_to_four, pin_gradient_ascent_baseline,
+                        pin_solve_weak_duality_lp,
                         pin_solve_monotone_rearrangement, pin_solve_gaussians_bures]
 
 
