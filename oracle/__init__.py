@@ -18,7 +18,9 @@ Functions and the passage each follows:
   neg_laplacian       the discrete Neumann Laplacian the Poisson solve inverts
   transport_map       Lemma 2.2(ii)
   pushforward         Section 2.1 pushforward, Lemma 3.1
-  solve               Algorithm 1 with the step rule of Section 4.2
+  ctransform_p        the c-transform of a separable power cost (Section 5)
+  solve               Algorithm 1 with the step rule of Section 4.2 (quadratic
+                      or separable power cost; or the gradient-ascent baseline)
   interpolate         displacement interpolation, Section 4.3
   w2_gradient         envelope theorem on eq. (symmetric_dual)
 """
@@ -64,6 +66,9 @@ def _configure(lib):
     lib.bfm_oracle_neg_laplacian.argtypes = [_DP, _DP, ctypes.c_int, _IP]
     lib.bfm_oracle_map.argtypes = [_DP, _DP, ctypes.c_int, _IP]
     lib.bfm_oracle_pushforward.argtypes = [_DP, _DP, _DP, ctypes.c_int, _IP]
+    lib.bfm_oracle_ctransform_p.argtypes = [_DP, _DP, ctypes.c_int, _IP, _DP]
+    lib.bfm_oracle_map_p.argtypes = [_DP, _DP, ctypes.c_int, _IP, _DP]
+    lib.bfm_oracle_pushforward_p.argtypes = [_DP, _DP, _DP, ctypes.c_int, _IP, _DP]
     lib.bfm_oracle_solve.argtypes = [_DP, _DP, ctypes.c_int, _IP, ctypes.c_double,
                                      ctypes.c_int, _DP, _DP, _DP, _DP, _DP, _DP,
                                      _DP, _DP, _DP]
@@ -159,21 +164,51 @@ def neg_laplacian(u) -> np.ndarray:
     return out
 
 
-def transport_map(psi) -> np.ndarray:
-    """T(x) = x - grad psi(x), clamped to the box of cell centres; shape (d, *grid)."""
-    psi = _f64(psi)
-    nd, n = _grid(psi.shape)
-    out = np.empty((nd,) + psi.shape)
-    assert _load().bfm_oracle_map(_ptr(psi), _ptr(out), nd, n) == 0
+def _exponents(p, nd):
+    """Per-axis exponents of the separable power cost as a double[3] (axis 0 first)."""
+    q = [float(x) for x in p] + [2.0] * (3 - len(p))
+    assert len(p) == nd and all(x > 1.0 for x in p)
+    return np.array(q, dtype=np.float64)
+
+
+def ctransform_p(phi, p) -> np.ndarray:
+    """phi^c for the separable power cost sum_a |y_a - x_a|^{p_a}/p_a (Section 5,
+    eq. p_costs), by dimension splitting with brute-force lines; p lists the
+    exponents from axis 0 (x) on."""
+    phi = _f64(phi)
+    out = np.empty_like(phi)
+    nd, n = _grid(phi.shape)
+    pe = _exponents(p, nd)
+    assert _load().bfm_oracle_ctransform_p(_ptr(phi), _ptr(out), nd, n, _ptr(pe)) == 0
     return out
 
 
-def pushforward(psi, mu) -> np.ndarray:
-    """rho = (x - grad psi)#mu with a multilinear deposit (density values)."""
+def transport_map(psi, p=None) -> np.ndarray:
+    """T(x) = x - (grad h)^{-1}(grad psi(x)) (the identity for the quadratic
+    cost, sign(w)|w|^{1/(p_a-1)} per axis for a power cost), clamped to the box
+    of cell centres; shape (d, *grid)."""
+    psi = _f64(psi)
+    nd, n = _grid(psi.shape)
+    out = np.empty((nd,) + psi.shape)
+    if p is None:
+        assert _load().bfm_oracle_map(_ptr(psi), _ptr(out), nd, n) == 0
+    else:
+        pe = _exponents(p, nd)
+        assert _load().bfm_oracle_map_p(_ptr(psi), _ptr(out), nd, n, _ptr(pe)) == 0
+    return out
+
+
+def pushforward(psi, mu, p=None) -> np.ndarray:
+    """rho = T#mu with the map above and a multilinear deposit (density values)."""
     psi, mu = _f64(psi), _f64(mu)
     rho = np.empty_like(mu)
     nd, n = _grid(mu.shape)
-    assert _load().bfm_oracle_pushforward(_ptr(psi), _ptr(mu), _ptr(rho), nd, n) == 0
+    if p is None:
+        assert _load().bfm_oracle_pushforward(_ptr(psi), _ptr(mu), _ptr(rho), nd, n) == 0
+    else:
+        pe = _exponents(p, nd)
+        assert _load().bfm_oracle_pushforward_p(_ptr(psi), _ptr(mu), _ptr(rho), nd, n,
+                                                _ptr(pe)) == 0
     return rho
 
 
@@ -191,10 +226,11 @@ DEFAULTS = dict(beta1=0.25, beta2=0.75, alpha1=1.25, alpha2=0.8, sigma0=0.0,
 
 
 def solve(mu, nu, tol: float = 1e-6, max_iter: int = 300, ct_mode: str = "linear",
-          dct_mode: str = "fft", method: str = "bfm", **opts) -> dict:
+          dct_mode: str = "fft", method: str = "bfm", p=None, **opts) -> dict:
     """Algorithm 1 with the step rule of Section 4.2, in FP64 (method "bfm"),
     or the H1-dot gradient ascent on J it is compared with in Section 5
-    (method "ga": phi += sigma grad J(phi), then phi = phi^cc).
+    (method "ga": phi += sigma grad J(phi), then phi = phi^cc).  p: exponents
+    of a separable power cost (axis 0 first; None: the quadratic cost).
 
     Returns phi, psi (= phi^c), map (d, *grid), w2sq (= 2 J(phi)), iters,
     converged, dual / resid / sigma logs (length iters+1) and the half-step
@@ -206,8 +242,10 @@ def solve(mu, nu, tol: float = 1e-6, max_iter: int = 300, ct_mode: str = "linear
     optv = np.array([o["beta1"], o["beta2"], o["alpha1"], o["alpha2"], o["sigma0"],
                      o["sigma_min"], {"brute": 0, "linear": 1}[ct_mode],
                      {"definition": 0, "fft": 1}[dct_mode],
-                     {"bfm": 0, "ga": 1}[method]], dtype=np.float64)
+                     {"bfm": 0, "ga": 1}[method], 0.0, 0.0, 0.0], dtype=np.float64)
     nd, n = _grid(mu.shape)
+    if p is not None:
+        optv[9:12] = _exponents(p, nd)
     phi = np.empty_like(mu)
     psi = np.empty_like(mu)
     tmap = np.empty((nd,) + mu.shape)

@@ -194,6 +194,57 @@ int bfm_oracle_ctransform(const double *phi, double *out, int ndim, const int *n
 }
 
 /*
+ * Separable power costs (Section 5, eq. p_costs): c(x,y) = sum_a h_a(y_a - x_a)
+ * with h_a(z) = |z|^{p_a} / p_a, p_a > 1.  The c-transform splits along the
+ * axes exactly as for the quadratic cost (Section 4.1, dimension splitting);
+ * each 1-D pass is the minimum over the grid points of the line, O(n^2).
+ */
+static double hpow(double z, double p) { return pow(fabs(z), p) / p; }
+
+static void line_brute_p(const double *f, double *u, int n, double h, double p)
+{
+    for (int i = 0; i < n; i++) {
+        double x = (i + 0.5) * h;
+        double best = INFINITY;
+        for (int j = 0; j < n; j++) {
+            double v = hpow((j + 0.5) * h - x, p) + f[j];
+            if (v < best) best = v;
+        }
+        u[i] = best;
+    }
+}
+
+int bfm_oracle_ctransform_p(const double *phi, double *out, int ndim, const int *n, const double *p)
+{
+    grid_t g;
+    if (make_grid(ndim, n, &g)) return -1;
+    double *cur = (double *)malloc(sizeof(double) * g.N);
+    if (!cur) return -2;
+    for (long i = 0; i < g.N; i++) cur[i] = -phi[i];
+    for (int a = 0; a < ndim; a++) {
+        int na = g.n[a];
+        long L = n_lines(&g, a);
+        long s = g.stride[a];
+        #pragma omp parallel
+        {
+            double *fin = (double *)malloc(sizeof(double) * na);
+            double *fo = (double *)malloc(sizeof(double) * na);
+            #pragma omp for schedule(static)
+            for (long l = 0; l < L; l++) {
+                long b = line_base(&g, a, l);
+                for (int i = 0; i < na; i++) fin[i] = cur[b + i * s];
+                line_brute_p(fin, fo, na, g.h[a], p[a]);
+                for (int i = 0; i < na; i++) cur[b + i * s] = fo[i];
+            }
+            free(fin); free(fo);
+        }
+    }
+    memcpy(out, cur, sizeof(double) * g.N);
+    free(cur);
+    return 0;
+}
+
+/*
  * phi^c by the definition with no splitting (Definition 2.1): the minimum
  * over every grid point y of |x-y|^2/2 - phi(y).  O(N^2); tiny grids only.
  */
@@ -414,7 +465,20 @@ int bfm_oracle_neg_laplacian(const double *u, double *out, int ndim, const int *
  * cell of a line; T is clamped to the box of cell centres [h/2, 1-h/2]^d so
  * that no mass leaves the grid.  out[a*N + p] = T_a(x_p).
  */
+int bfm_oracle_map_p(const double *psi, double *out, int ndim, const int *n, const double *pw);
+
 int bfm_oracle_map(const double *psi, double *out, int ndim, const int *n)
+{
+    return bfm_oracle_map_p(psi, out, ndim, n, NULL);
+}
+
+/*
+ * The same map for the separable power cost (Lemma 2.2(ii)):
+ * T_a(x) = x_a - (h_a')^{-1}(d psi / d x_a) with (h_a')^{-1}(w) =
+ * sign(w) |w|^{1/(p_a - 1)} (pw holds the exponents p_a).  pw == NULL: the
+ * quadratic cost.
+ */
+int bfm_oracle_map_p(const double *psi, double *out, int ndim, const int *n, const double *pw)
 {
     grid_t g;
     if (make_grid(ndim, n, &g)) return -1;
@@ -432,7 +496,9 @@ int bfm_oracle_map(const double *psi, double *out, int ndim, const int *n)
             else if (i == na - 1) grad = (psi[p] - psi[p - s]) / h;
             else grad = (psi[p + s] - psi[p - s]) / (2.0 * h);
             double x = (i + 0.5) * h;
-            double t = x - grad;
+            double disp = grad;
+            if (pw) disp = (grad < 0 ? -1.0 : 1.0) * pow(fabs(grad), 1.0 / (pw[a] - 1.0));
+            double t = x - disp;
             if (t < 0.5 * h) t = 0.5 * h;
             if (t > 1.0 - 0.5 * h) t = 1.0 - 0.5 * h;
             out[a * g.N + p] = t;
@@ -448,12 +514,22 @@ int bfm_oracle_map(const double *psi, double *out, int ndim, const int *n)
  * multilinear interpolation weights; rho is the received mass divided by hd.
  * Because T is clamped to the box of cell centres the mass is conserved.
  */
+int bfm_oracle_pushforward_p(const double *psi, const double *mu, double *rho, int ndim,
+                             const int *n, const double *pw);
+
 int bfm_oracle_pushforward(const double *psi, const double *mu, double *rho, int ndim, const int *n)
+{
+    return bfm_oracle_pushforward_p(psi, mu, rho, ndim, n, NULL);
+}
+
+/* The same deposit with the map of the separable power cost (pw == NULL: quadratic). */
+int bfm_oracle_pushforward_p(const double *psi, const double *mu, double *rho, int ndim,
+                             const int *n, const double *pw)
 {
     grid_t g;
     if (make_grid(ndim, n, &g)) return -1;
     double *T = (double *)malloc(sizeof(double) * g.N * ndim);
-    bfm_oracle_map(psi, T, ndim, n);
+    bfm_oracle_map_p(psi, T, ndim, n, pw);
     for (long p = 0; p < g.N; p++) rho[p] = 0.0;
     for (long p = 0; p < g.N; p++) {
         if (mu[p] == 0.0) continue;
@@ -495,7 +571,16 @@ typedef struct {
     int ct_mode;                          /* 0 brute, 1 Legendre/linear */
     int dct_mode;                         /* 0 definition, 1 FFT */
     int method;                           /* 0 back-and-forth, 1 gradient ascent on J */
+    int power;                            /* 1: separable power cost with exponents p */
+    double p[3];
 } oracle_opts;
+
+/* c-transform, pushforward and map of the cost in use */
+static void ct_cost(const double *in, double *out, int ndim, const int *n, const oracle_opts *o)
+{
+    if (o->power) bfm_oracle_ctransform_p(in, out, ndim, n, o->p);
+    else bfm_oracle_ctransform(in, out, ndim, n, o->ct_mode);
+}
 
 typedef struct {
     int iters;        /* completed back-and-forth iterations */
@@ -557,12 +642,18 @@ int bfm_oracle_solve(const double *mu_in, const double *nu_in, int ndim, const i
 {
     grid_t g;
     if (make_grid(ndim, n, &g)) return -1;
-    oracle_opts o = {0.25, 0.75, 1.25, 0.8, 0.0, 0.01, 1, 1, 0};
+    oracle_opts o = {0.25, 0.75, 1.25, 0.8, 0.0, 0.01, 1, 1, 0, 0, {2.0, 2.0, 2.0}};
     if (opt_in) {
         o.beta1 = opt_in[0]; o.beta2 = opt_in[1]; o.alpha1 = opt_in[2]; o.alpha2 = opt_in[3];
         o.sigma0 = opt_in[4]; o.sigma_min = opt_in[5];
         o.ct_mode = (int)opt_in[6]; o.dct_mode = (int)opt_in[7]; o.method = (int)opt_in[8];
+        /* opt_in[9..11] > 0: exponents of the separable power cost */
+        if (opt_in[9] > 0) {
+            o.power = 1;
+            for (int a = 0; a < 3; a++) o.p[a] = opt_in[9 + a];
+        }
     }
+    const double *pc = o.power ? o.p : NULL;
     long N = g.N;
     double *mu = malloc(sizeof(double) * N), *nu = malloc(sizeof(double) * N);
     double *phi = calloc(N, sizeof(double)), *psi = calloc(N, sizeof(double));
@@ -591,9 +682,9 @@ int bfm_oracle_solve(const double *mu_in, const double *nu_in, int ndim, const i
      * Algorithm 1 (half[3n] = J(phi_{n+1/2})).
      */
     if (o.method == 1) for (it = 0; it <= max_iter; it++) {
-        bfm_oracle_ctransform(phi, tmp, ndim, n, o.ct_mode);          /* phi_n^c */
+        ct_cost(phi, tmp, ndim, n, &o);          /* phi_n^c */
         Jold = dot_hd(&g, phi, nu) + dot_hd(&g, tmp, mu);
-        bfm_oracle_pushforward(tmp, mu, rho, ndim, n);
+        bfm_oracle_pushforward_p(tmp, mu, rho, ndim, n, pc);
         for (long i = 0; i < N; i++) f[i] = nu[i] - rho[i];
         double G;
         bfm_oracle_poisson(f, gr, ndim, n, o.dct_mode, &G);
@@ -604,17 +695,17 @@ int bfm_oracle_solve(const double *mu_in, const double *nu_in, int ndim, const i
         if (r < tol) { conv = 1; break; }
         if (it == max_iter) break;
         for (long i = 0; i < N; i++) phi[i] += sigma * gr[i];        /* phi_{n+1/2} */
-        bfm_oracle_ctransform(phi, psi, ndim, n, o.ct_mode);          /* phi_{n+1/2}^c */
+        ct_cost(phi, psi, ndim, n, &o);          /* phi_{n+1/2}^c */
         double Jnew = dot_hd(&g, phi, nu) + dot_hd(&g, psi, mu);
         sigma = step_rule(sigma, Jnew - Jold, G, &o);
-        bfm_oracle_ctransform(psi, phi, ndim, n, o.ct_mode);          /* phi_{n+1} */
+        ct_cost(psi, phi, ndim, n, &o);          /* phi_{n+1} */
         if (half) { half[3 * it + 0] = Jnew; half[3 * it + 1] = 0.0; half[3 * it + 2] = 0.0; }
     }
     if (o.method == 0) for (it = 0; it <= max_iter; it++) {
         /* phi-half step */
-        bfm_oracle_ctransform(phi, tmp, ndim, n, o.ct_mode);          /* psi~ = phi^c */
+        ct_cost(phi, tmp, ndim, n, &o);          /* psi~ = phi^c */
         Jold = dot_hd(&g, phi, nu) + dot_hd(&g, tmp, mu);
-        bfm_oracle_pushforward(tmp, mu, rho, ndim, n);
+        bfm_oracle_pushforward_p(tmp, mu, rho, ndim, n, pc);
         for (long i = 0; i < N; i++) f[i] = nu[i] - rho[i];
         double G;
         bfm_oracle_poisson(f, gr, ndim, n, o.dct_mode, &G);
@@ -625,18 +716,18 @@ int bfm_oracle_solve(const double *mu_in, const double *nu_in, int ndim, const i
         if (r < tol) { conv = 1; break; }
         if (it == max_iter) break;
         for (long i = 0; i < N; i++) phi[i] += sigma * gr[i];
-        bfm_oracle_ctransform(phi, psi, ndim, n, o.ct_mode);          /* psi_{n+1/2} */
+        ct_cost(phi, psi, ndim, n, &o);          /* psi_{n+1/2} */
         double Jnew = dot_hd(&g, phi, nu) + dot_hd(&g, psi, mu);
         sigma = step_rule(sigma, Jnew - Jold, G, &o);
         /* psi-half step */
-        bfm_oracle_ctransform(psi, tmp, ndim, n, o.ct_mode);          /* phi~ = psi^c */
+        ct_cost(psi, tmp, ndim, n, &o);          /* phi~ = psi^c */
         double Iold = dot_hd(&g, tmp, nu) + dot_hd(&g, psi, mu);
-        bfm_oracle_pushforward(tmp, nu, rho, ndim, n);
+        bfm_oracle_pushforward_p(tmp, nu, rho, ndim, n, pc);
         for (long i = 0; i < N; i++) f[i] = mu[i] - rho[i];
         double G2;
         bfm_oracle_poisson(f, gr, ndim, n, o.dct_mode, &G2);
         for (long i = 0; i < N; i++) psi[i] += sigma * gr[i];
-        bfm_oracle_ctransform(psi, phi, ndim, n, o.ct_mode);          /* phi_{n+1} */
+        ct_cost(psi, phi, ndim, n, &o);          /* phi_{n+1} */
         double Inew = dot_hd(&g, phi, nu) + dot_hd(&g, psi, mu);
         sigma = step_rule(sigma, Inew - Iold, G2, &o);
         if (half) {
@@ -646,7 +737,7 @@ int bfm_oracle_solve(const double *mu_in, const double *nu_in, int ndim, const i
     /* outputs: phi_n and its c-transform, the map T = x - grad phi_n^c */
     memcpy(phi_out, phi, sizeof(double) * N);
     memcpy(psi_out, tmp, sizeof(double) * N);
-    if (map_out) bfm_oracle_map(tmp, map_out, ndim, n);
+    if (map_out) bfm_oracle_map_p(tmp, map_out, ndim, n, pc);
     if (info_out) {
         info_out[0] = it;
         info_out[1] = conv;

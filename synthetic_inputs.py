@@ -16,7 +16,8 @@ order written):
   workload_batched_uneven    128 problems, sides in {64,128,256,512}
   workload_loss_pairs_256    32 pairs of Gaussian mixtures, 256x256
 and the closed-form shapes of the paper's Section 4.3 (translated discs and
-balls, one square to four squares, one cube to eight cubes).
+balls, one square to four squares, one cube to eight cubes) and the two-disc
+pair of its power-cost experiment (Section 5).
 """
 from __future__ import annotations
 
@@ -119,6 +120,14 @@ def cube_to_eight(n):
             for k in (0, 1):
                 c = (3 / 16 + 5 * i / 8, 3 / 16 + 5 * j / 8, 3 / 16 + 5 * k / 8)
                 nu += box((n, n, n), c, 0.125)
+    return normalise(mu), normalise(nu)
+
+
+def diagonal_to_antidiagonal_discs(n):
+    """Section 5, separable power costs: discs r=1/8 at (1/4,1/4) and (3/4,3/4)
+    -> discs r=1/8 at (1/4,3/4) and (3/4,1/4)."""
+    mu = ball((n, n), (0.25, 0.25), 0.125) + ball((n, n), (0.75, 0.75), 0.125)
+    nu = ball((n, n), (0.25, 0.75), 0.125) + ball((n, n), (0.75, 0.25), 0.125)
     return normalise(mu), normalise(nu)
 
 

@@ -229,6 +229,66 @@ def pin_gradient_ascent_baseline():
     assert np.all(ga["dual"] <= gold["exact_cost"] + 1e-12)   # weak duality
 
 
+# --- separable power costs (Section 5, eq. p_costs) ------------------------------
+
+def pin_power_cost_definition_and_p2():
+    """The power-cost c-transform by dimension splitting equals the minimum of
+    sum_a |x_a - y_a|^{p_a}/p_a - phi(y) over every grid point y (brute force
+    on a tiny grid, no splitting); p = (2, 2) reproduces the quadratic
+    c-transform and solve."""
+    shape = (5, 6)                       # (n1, n0)
+    phi = si.random_field(shape, 21, 0.2)
+    p = (1.3, 2.7)
+    x, y = si.centres((6, 5))
+    X, Y = x.ravel(), y.ravel()
+    cost = (np.abs(X[:, None] - X[None, :]) ** p[0] / p[0] +
+            np.abs(Y[:, None] - Y[None, :]) ** p[1] / p[1])
+    want = np.min(cost - phi.ravel()[None, :], axis=1).reshape(shape)
+    assert np.max(np.abs(oracle.ctransform_p(phi, p) - want)) < 1e-14
+    phi2 = si.random_field((20, 24), 22, 0.1)
+    assert np.max(np.abs(oracle.ctransform_p(phi2, (2.0, 2.0)) - oracle.ctransform(phi2))) < 1e-14
+    mu, nu = si.translated_discs(32)
+    a = oracle.solve(mu, nu, tol=0.0, max_iter=5)
+    b = oracle.solve(mu, nu, tol=0.0, max_iter=5, p=(2.0, 2.0))
+    assert np.max(np.abs(a["dual"] - b["dual"])) < 1e-14
+
+
+def pin_power_cost_translation():
+    """A translation by a is optimal for any strictly convex cost h(y - x):
+    the two discs of Table 1 cost h((1/2, 1/2)) = sum_a (1/2)^{p_a} / p_a, and
+    the map moves mu's cells by a."""
+    mu, nu = si.translated_discs(48)
+    p = (1.5, 2.5)
+    exact = 0.5 ** p[0] / p[0] + 0.5 ** p[1] / p[1]
+    r = oracle.solve(mu, nu, tol=0.0, max_iter=15, p=p)
+    assert abs(r["dual"][-1] - exact) < 1e-10
+    assert np.all(r["dual"] <= exact + 1e-12)
+    x, y = si.centres((48, 48))
+    m = mu > 0
+    inner = m & (np.hypot(x - 0.25, y - 0.25) < 0.125 - 2.0 / 48)   # away from the edge cells
+    assert np.max(np.abs(r["map"][0][inner] - x[inner] - 0.5)) < 1.0 / 48
+    assert np.max(np.abs(r["map"][1][inner] - y[inner] - 0.5)) < 1.0 / 48
+
+
+def pin_power_cost_direction_of_transport():
+    """Section 5's two-disc example: with p = (2, 2) each disc of mu splits
+    evenly between the two discs of nu; with p = (1.1, 3) horizontal moves
+    are so expensive that all mass moves vertically by 1/2, at cost
+    (1/2)^3 / 3 = 1/24."""
+    mu, nu = si.diagonal_to_antidiagonal_discs(48)
+    x, y = si.centres((48, 48))
+    m = mu > 0
+    def vertical(p):
+        r = oracle.solve(mu, nu, tol=0.0, max_iter=30, p=p)
+        dx, dy = r["map"][0] - x, r["map"][1] - y
+        return np.sum(mu[m] * (np.abs(dy[m]) > np.abs(dx[m]))) / np.sum(mu[m]), r
+    v2, _ = vertical((2.0, 2.0))
+    assert abs(v2 - 0.5) < 0.05
+    v, r = vertical((1.1, 3.0))
+    assert v > 0.99
+    assert abs(r["dual"][-1] - 1.0 / 24.0) < 1e-8
+
+
 def pin_solve_chain_invariants():
     """Section 3.2: a c-transform never lowers the dual value, so
     J(phi_{n+1/2}) <= I(psi_{n+1/2}) and I(psi_{n+1}) <= J(phi_{n+1})."""
@@ -329,6 +389,8 @@ FAST_PINS = [
     pin_solve_chain_invariants, pin_step_rule_constants, pin_interpolate_translation,
 ]
 ALL_PINS = FAST_PINS + [pin_solve_square_to_four, pin_gradient_ascent_baseline,
+                        pin_power_cost_definition_and_p2, pin_power_cost_translation,
+                        pin_power_cost_direction_of_transport,
                         pin_solve_weak_duality_lp,
                         pin_solve_monotone_rearrangement, pin_solve_gaussians_bures]
 
