@@ -32,7 +32,7 @@ MUTANTS = [
     ("fft_reorder", "buf[n - 1 - q] = x[2 * q + 1];", "buf[n - 1 - q] = x[2 * q];", 0),
     ("eig_factor", "lam += 4.0 * g.n[a] * (double)g.n[a] * s * s;", "lam += 2.0 * g.n[a] * (double)g.n[a] * s * s;", 0),
     ("eig_angle", "double s = sin(M_PI * k / (2.0 * g.n[a]));", "double s = sin(M_PI * k / g.n[a]);", 0),
-    ("map_sign", "double t = x - grad;", "double t = x + grad;", 0),
+    ("map_sign", "double t = x - disp;", "double t = x + disp;", 0),
     ("central_difference", "grad = (psi[p + s] - psi[p - s]) / (2.0 * h);", "grad = (psi[p + s] - psi[p - s]) / h;", 0),
     ("onesided_difference", "grad = (psi[p + s] - psi[p]) / h;", "grad = (psi[p + s] - psi[p]) / (2.0 * h);", 0),
     ("bilinear_swap", "w *= up ? w1[a] : (1.0 - w1[a]);", "w *= up ? (1.0 - w1[a]) : w1[a];", 0),
@@ -40,7 +40,10 @@ MUTANTS = [
     ("step_rule_inverted", "if (gain < o->beta1 * sigma * G) {", "if (gain > o->beta1 * sigma * G) {", 0),
     ("sigma0_constant", "8.0 * fmin(1.0 / mx_mu, 1.0 / mx_nu)", "4.0 * fmin(1.0 / mx_mu, 1.0 / mx_nu)", 0),
     ("w2_factor", "info_out[2] = 2.0 * Jold;", "info_out[2] = Jold;", 0),
-    ("psi_half_measure", "bfm_oracle_pushforward(tmp, nu, rho, ndim, n);", "bfm_oracle_pushforward(tmp, mu, rho, ndim, n);", 0),
+    ("psi_half_measure", "bfm_oracle_pushforward_p(tmp, nu, rho, ndim, n, pc);",
+     "bfm_oracle_pushforward_p(tmp, mu, rho, ndim, n, pc);", 0),
+    ("power_cost_exponent", "return pow(fabs(z), p) / p;", "return pow(fabs(z), p) / 2.0;", 0),
+    ("power_map_inverse_gradient", "pow(fabs(grad), 1.0 / (pw[a] - 1.0))", "pow(fabs(grad), pw[a] - 1.0)", 0),
     ("psi_half_residual", "f[i] = mu[i] - rho[i];", "f[i] = nu[i] - rho[i];", 0),
     ("update_sign", "phi[i] += sigma * gr[i];", "phi[i] -= sigma * gr[i];", 0),
     ("dual_uses_wrong_density", "Jold = dot_hd(&g, phi, nu) + dot_hd(&g, tmp, mu);",
