@@ -58,8 +58,10 @@ typedef enum {
 
 typedef enum { BFM_FP32 = 0, BFM_FP64 = 1 } bfm_precision;
 
-/* Only the quadratic cost |x-y|^2/2 of Section 4.3 is implemented. */
-typedef enum { BFM_COST_QUADRATIC = 0 } bfm_cost;
+/* Costs: the quadratic cost |x-y|^2/2 of Section 4.3, and the separable power
+ * costs of Section 5 (eq. p_costs), c(x,y) = sum_a |y_a - x_a|^{p_a} / p_a with
+ * 1 < p_a <= 16 given in bfm_options.cost_p (axis 0 first). */
+typedef enum { BFM_COST_QUADRATIC = 0, BFM_COST_POWER = 1 } bfm_cost;
 
 typedef struct {
     int ndim;       /* 2 or 3 */
@@ -78,7 +80,7 @@ typedef enum { BFM_BACK_AND_FORTH = 0, BFM_GRADIENT_ASCENT = 1 } bfm_method;
 /* Step-size rule of Section 4.2 and loop control.  bfm_default_options()
  * fills the paper's values: beta1 = 1/4, beta2 = 3/4, alpha1 = 5/4,
  * alpha2 = 4/5, sigma0 <= 0 meaning 8 min(1/|mu|_inf, 1/|nu|_inf),
- * sigma_min = 0.01, and method = BFM_BACK_AND_FORTH. */
+ * sigma_min = 0.01, method = BFM_BACK_AND_FORTH and cost_p = {0, 0, 0}. */
 typedef struct {
     double beta1, beta2, alpha1, alpha2;
     double sigma0;
@@ -86,6 +88,8 @@ typedef struct {
     int poll_every;          /* host reads the device convergence flag every k iterations (default 4) */
     int warm_start;          /* nonzero: result->phi holds the initial phi on entry (else phi_0 = 0) */
     int method;              /* bfm_method */
+    double cost_p[3];        /* BFM_COST_POWER: the exponents p_a (axis 0 first); all 0 for
+                                the quadratic cost */
 } bfm_options;
 
 typedef struct {
@@ -124,7 +128,10 @@ size_t bfm_workspace_bytes(const bfm_grid *grid, bfm_precision prec, int max_ite
 
 /*
  * Algorithm 1 (the back-and-forth method) with the step-size rule of
- * Section 4.2, quadratic cost.  Per iteration n (4 c-transforms and 2
+ * Section 4.2 (or opt->method's gradient ascent).  cost: BFM_COST_QUADRATIC
+ * (opt->cost_p all 0), or BFM_COST_POWER with the exponents in opt->cost_p;
+ * for a power cost T(x) = x - (grad h)^{-1}(grad psi~) and the c-transforms
+ * are those of bfm_ctransform_power.  Per iteration n (4 c-transforms and 2
  * Poisson solves, as counted in Section 4.3):
  *   phi-half: psi~ = phi^c; J(phi) (eq. (defJ)); rho = T_phi # mu with
  *             T(x) = x - grad psi~ (Lemma 2.2(ii), Lemma 3.1); g =
@@ -196,7 +203,8 @@ bfm_status bfm_profile_end(double *ms_by_kind, int *launches_by_kind, int nkinds
  * opt->poll_every iterations is captured once as a CUDA graph and replayed
  * until every problem has stopped.  Returns BFM_OK when all converged,
  * BFM_NOT_CONVERGED when some reached max_iter (outs[p].converged says which).
- * opt->warm_start is not supported here.  Synchronises `stream`.
+ * opt->warm_start, the gradient-ascent method and power costs are not
+ * supported here (BFM_ERR_UNSUPPORTED).  Synchronises `stream`.
  */
 size_t bfm_workspace_bytes_batched(int nprob, const bfm_grid *grids, bfm_precision prec,
                                    int max_iter);
@@ -291,6 +299,22 @@ bfm_status bfm_poisson_noalloc(const void *f, void *g, const bfm_grid *grid, bfm
  */
 bfm_status bfm_map(const void *psi, void *map, const bfm_grid *grid, bfm_precision prec,
                    void *stream);
+
+/*
+ * The c-transform (Definition 2.1) and the map (Lemma 2.2(ii)) of the
+ * separable power cost c(x,y) = sum_a |y_a - x_a|^{p_a}/p_a (Section 5, eq.
+ * p_costs; the fast c-transform of Section 4.1): phi^c by dimension splitting,
+ * each 1-D pass by the divide-and-conquer over the monotone minimiser, and
+ * T_a(x) = x_a - sign(w_a)|w_a|^{1/(p_a - 1)} with w = grad psi by central
+ * differences (one-sided at the first and last cell), clamped as in bfm_map.
+ * p: HOST, ndim exponents with 1 < p_a <= 16 (axis 0 first); other arguments
+ * as bfm_ctransform and bfm_map.  A line must fit in shared memory (up to
+ * 8192 FP32 or 4096 FP64 cells); longer lines return BFM_ERR_UNSUPPORTED.
+ */
+bfm_status bfm_ctransform_power(const void *phi, void *out, const bfm_grid *grid,
+                                bfm_precision prec, const double *p, void *stream);
+bfm_status bfm_map_power(const void *psi, void *map, const bfm_grid *grid, bfm_precision prec,
+                         const double *p, void *stream);
 
 /*
  * Pushforward rho = T # mu (Section 2.1; the first variation of Lemma 3.1)

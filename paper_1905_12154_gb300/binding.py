@@ -31,6 +31,7 @@ BFM_FP64 = 1
 BFM_BACK_AND_FORTH = 0
 BFM_GRADIENT_ASCENT = 1
 BFM_COST_QUADRATIC = 0
+BFM_COST_POWER = 1
 
 
 class bfm_grid(ctypes.Structure):
@@ -42,7 +43,7 @@ class bfm_options(ctypes.Structure):
                 ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double),
                 ("sigma0", ctypes.c_double), ("sigma_min", ctypes.c_double),
                 ("poll_every", ctypes.c_int), ("warm_start", ctypes.c_int),
-                ("method", ctypes.c_int)]
+                ("method", ctypes.c_int), ("cost_p", ctypes.c_double * 3)]
 
 
 class bfm_result(ctypes.Structure):
@@ -67,6 +68,7 @@ _lib = None
 
 _P = ctypes.c_void_p
 _GP = ctypes.POINTER(bfm_grid)
+_DP3 = ctypes.POINTER(ctypes.c_double * 3)
 _SIGS = {
     "bfm_default_options": (None, [ctypes.POINTER(bfm_options)]),
     "bfm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -81,6 +83,8 @@ _SIGS = {
                                       ctypes.c_int, ctypes.POINTER(bfm_options), _P,
                                       ctypes.c_size_t, _P, ctypes.POINTER(bfm_result)]),
     "bfm_ctransform": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, _P]),
+    "bfm_ctransform_power": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, _DP3, _P]),
+    "bfm_map_power": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, _DP3, _P]),
     "bfm_poisson": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    _P, ctypes.c_size_t, _P]),
     "bfm_poisson_noalloc": (ctypes.c_int, [_P, _P, _GP, ctypes.c_int,
@@ -208,15 +212,31 @@ METHODS = {"bfm": BFM_BACK_AND_FORTH, "back_and_forth": BFM_BACK_AND_FORTH,
 
 def _options(**kw) -> bfm_options:
     """bfm_options with the paper's defaults, overridden by keyword (method may
-    be given as "bfm" / "ga")."""
+    be given as "bfm" / "ga"; p = exponents of a separable power cost)."""
     o = bfm_options()
     lib().bfm_default_options(ctypes.byref(o))
     for k, v in kw.items():
-        if v is not None:
-            if k == "method" and isinstance(v, str):
-                v = METHODS[v]
-            setattr(o, k, v)
+        if v is None:
+            continue
+        if k == "p":
+            vals = [float(x) for x in v]
+            o.cost_p = (ctypes.c_double * 3)(*(vals + [0.0] * (3 - len(vals))))
+            continue
+        if k == "method" and isinstance(v, str):
+            v = METHODS[v]
+        setattr(o, k, v)
     return o
+
+
+def _cost(opts) -> int:
+    """The bfm_cost of a call: the separable power cost when p is given."""
+    return BFM_COST_POWER if opts.get("p") is not None else BFM_COST_QUADRATIC
+
+
+def _exponents(p, nd):
+    if p is None or len(p) != nd:
+        raise ValueError(f"p needs one exponent per axis ({nd})")
+    return (ctypes.c_double * 3)(*([float(x) for x in p] + [0.0] * (3 - nd)))
 
 
 # --- entry points ----------------------------------------------------------------
@@ -233,14 +253,20 @@ def bfm_poisson_workspace_bytes(shape, prec: int) -> int:
     return int(lib().bfm_poisson_workspace_bytes(ctypes.byref(grid_of(shape)), prec))
 
 
-def bfm_ctransform(phi, out=None):
-    """out = phi^c on the grid (Definition 2.1, Section 4.1)."""
+def bfm_ctransform(phi, out=None, p=None):
+    """out = phi^c on the grid (Definition 2.1, Section 4.1); p: exponents of a
+    separable power cost (Section 5, axis 0 first), None for the quadratic cost."""
     import torch
     _dev(phi, "phi")
     out = torch.empty_like(phi) if out is None else _dev(out, "out")
     g = grid_of(phi.shape)
-    _check(lib().bfm_ctransform(phi.data_ptr(), out.data_ptr(), ctypes.byref(g), _prec(phi),
-                                _stream()), "bfm_ctransform")
+    if p is None:
+        _check(lib().bfm_ctransform(phi.data_ptr(), out.data_ptr(), ctypes.byref(g), _prec(phi),
+                                    _stream()), "bfm_ctransform")
+    else:
+        _check(lib().bfm_ctransform_power(phi.data_ptr(), out.data_ptr(), ctypes.byref(g),
+                                          _prec(phi), _exponents(p, phi.dim()), _stream()),
+               "bfm_ctransform_power")
     return out
 
 
@@ -273,15 +299,20 @@ def bfm_poisson_noalloc(f, out=None):
     return out, G.value
 
 
-def bfm_map(psi, out=None):
-    """T(x) = x - grad psi(x) (Lemma 2.2(ii)); shape (ndim, *grid)."""
+def bfm_map(psi, out=None, p=None):
+    """T(x) = x - (grad h)^{-1}(grad psi(x)) (Lemma 2.2(ii)); shape (ndim, *grid);
+    p: exponents of a separable power cost, None for the quadratic cost."""
     import torch
     _dev(psi, "psi")
     nd = psi.dim()
     out = torch.empty((nd,) + tuple(psi.shape), dtype=psi.dtype, device=psi.device) if out is None else _dev(out, "out")
     g = grid_of(psi.shape)
-    _check(lib().bfm_map(psi.data_ptr(), out.data_ptr(), ctypes.byref(g), _prec(psi), _stream()),
-           "bfm_map")
+    if p is None:
+        _check(lib().bfm_map(psi.data_ptr(), out.data_ptr(), ctypes.byref(g), _prec(psi),
+                             _stream()), "bfm_map")
+    else:
+        _check(lib().bfm_map_power(psi.data_ptr(), out.data_ptr(), ctypes.byref(g), _prec(psi),
+                                   _exponents(p, nd), _stream()), "bfm_map_power")
     return out
 
 
@@ -338,7 +369,7 @@ def bfm_solve(mu, nu, tol: float = 1e-6, max_iter: int = 300, with_map: bool = T
     else:
         keep, ws, nb = _user_workspace(workspace)
     o = _options(**opts)
-    s = lib().bfm_solve(mu.data_ptr(), nu.data_ptr(), ctypes.byref(g), BFM_COST_QUADRATIC, prec,
+    s = lib().bfm_solve(mu.data_ptr(), nu.data_ptr(), ctypes.byref(g), _cost(opts), prec,
                         float(tol), int(max_iter), ctypes.byref(o), ws, nb, _stream(),
                         ctypes.byref(res))
     _check(s, "bfm_solve", ok=(BFM_OK, BFM_NOT_CONVERGED))
@@ -377,7 +408,7 @@ def bfm_solve_host(mu: np.ndarray, nu: np.ndarray, tol: float = 1e-6, max_iter: 
     else:
         keep, ws, nb = _user_workspace(workspace)
     o = _options(**opts)
-    s = lib().bfm_solve_host(mu.ctypes.data, nu.ctypes.data, ctypes.byref(g), BFM_COST_QUADRATIC,
+    s = lib().bfm_solve_host(mu.ctypes.data, nu.ctypes.data, ctypes.byref(g), _cost(opts),
                              prec, float(tol), int(max_iter), ctypes.byref(o), ws, nb, _stream(),
                              ctypes.byref(res))
     _check(s, "bfm_solve_host", ok=(BFM_OK, BFM_NOT_CONVERGED))
@@ -409,7 +440,7 @@ class BfmSolver:
         self._ws_keep, self._ws = _workspace(self.nbytes, mu.device)
         self._opts = _options(**opts)
         _check(lib().bfm_solver_init(mu.data_ptr(), nu.data_ptr(), ctypes.byref(self.grid),
-                                     BFM_COST_QUADRATIC, self.prec, float(tol), self.max_iter,
+                                     _cost(opts), self.prec, float(tol), self.max_iter,
                                      ctypes.byref(self._opts), self._ws, self.nbytes, _stream(),
                                      self.phi.data_ptr(), self.psi.data_ptr()),
                "bfm_solver_init")

@@ -477,6 +477,10 @@ extern "C" bfm_status bfm_solve_batched(int nprob, const void* const* mu, const 
         set_last_error("batched solves run the back-and-forth iteration only");
         return BFM_ERR_UNSUPPORTED;
     }
+    if (o.cost_p[0] != 0.0 || o.cost_p[1] != 0.0 || o.cost_p[2] != 0.0) {
+        set_last_error("batched solves use the quadratic cost only");
+        return BFM_ERR_UNSUPPORTED;
+    }
     if (!(o.beta1 > 0 && o.beta1 < o.beta2 && o.beta2 < 1 && o.alpha1 > 1 && o.alpha2 > 0 &&
           o.alpha2 < 1 && o.sigma_min >= 0))
         return BFM_ERR_INVALID_ARG;

@@ -108,4 +108,5 @@ extern "C" void bfm_default_options(bfm_options* o)
     o->poll_every = 4;
     o->warm_start = 0;
     o->method = BFM_BACK_AND_FORTH;
+    o->cost_p[0] = o->cost_p[1] = o->cost_p[2] = 0.0;
 }

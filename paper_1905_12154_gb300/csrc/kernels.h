@@ -60,12 +60,20 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
                            const double* sigma, double* part, const int* done,
                            cudaStream_t st, int* blocks_used);
 
-// scatter.cu
+// scatter.cu (p: exponents of a separable power cost, NULL for the quadratic cost)
 template <typename T>
 bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho,
-                              const int* done, cudaStream_t st);
+                              const int* done, cudaStream_t st, const double* p = nullptr);
 template <typename T>
-bfm_status launch_map(const Grid& g, const T* psi, T* map, cudaStream_t st);
+bfm_status launch_map(const Grid& g, const T* psi, T* map, cudaStream_t st,
+                      const double* p = nullptr);
+
+// ctpower.cu: one 1-D c-transform pass of the separable power cost along
+// `axis` with exponent p (same arguments as launch_ct_pass)
+template <typename T>
+bfm_status launch_ct_power_pass(const Grid& g, int axis, double p, const T* in, T* out, bool negate,
+                                const T* w_in, double* part_in, const T* w_out, double* part_out,
+                                const int* done, int max_blocks, cudaStream_t st, int* blocks_used);
 template <typename T>
 bfm_status launch_interpolate(const Grid& g, const T* map, const T* mu, double t, T* rho,
                               cudaStream_t st);

@@ -1,7 +1,9 @@
 // scatter.cu -- the map T(x) = x - grad psi(x) and the pushforward T # mu.
 //
-// Lemma 2.2(ii): for the quadratic cost the minimiser of the c-transform is
-// T(x) = x - grad phi^c(x).  Lemma 3.1: the first variation of J is
+// Lemma 2.2(ii): the minimiser of the c-transform is T(x) = x -
+// (grad h)^{-1}(grad phi^c(x)): x - grad phi^c(x) for the quadratic cost, and
+// per axis x_a - sign(w_a)|w_a|^{1/(p_a - 1)} (w = grad phi^c) for the
+// separable power cost of Section 5.  Lemma 3.1: the first variation of J is
 // nu - T # mu.  The pushforward (Section 2.1) is discretised by sending the
 // mass of every source cell to the 2^d cell centres around T(x) with
 // multilinear weights; T is clamped to the box of cell centres so mass is
@@ -18,15 +20,28 @@ struct GridDev {
     int n[3];
     long long s[3];
     long long N;
+    int power;            // separable power cost: (h_a')^{-1}(w) = sign(w)|w|^{q_a}
+    double q[3];          // q_a = 1 / (p_a - 1)
 };
 
-static GridDev dev_grid(const Grid& g)
+// p: the exponents of a separable power cost (axis 0 first), NULL for the
+// quadratic cost
+static GridDev dev_grid(const Grid& g, const double* p = nullptr)
 {
     GridDev d;
-    for (int a = 0; a < 3; ++a) { d.n[a] = g.n[a]; d.s[a] = g.stride[a]; }
+    for (int a = 0; a < 3; ++a) {
+        d.n[a] = g.n[a];
+        d.s[a] = g.stride[a];
+        d.q[a] = (p && a < g.ndim) ? 1.0 / (p[a] - 1.0) : 1.0;
+    }
     d.N = g.N;
+    d.power = p ? 1 : 0;
     return d;
 }
+
+template <typename T> __device__ __forceinline__ T pow_s(T x, T y);
+template <> __device__ __forceinline__ float pow_s<float>(float x, float y) { return powf(x, y); }
+template <> __device__ __forceinline__ double pow_s<double>(double x, double y) { return pow(x, y); }
 
 static int grid_blocks(long long N, int threads)
 {
@@ -39,13 +54,20 @@ static int grid_blocks(long long N, int threads)
 
 // position of T(x) along one axis, in cell-index units, clamped to [0, n-1]
 template <typename T>
-__device__ __forceinline__ T map_pos(const T* psi, long long idx, int i, int n, long long s)
+__device__ __forceinline__ T map_pos(const T* psi, long long idx, int i, int n, long long s,
+                                     int power, double q)
 {
+    T dpsi;                                   // psi difference per cell
+    if (i == 0)          dpsi = psi[idx + s] - psi[idx];
+    else if (i == n - 1) dpsi = psi[idx] - psi[idx - s];
+    else                 dpsi = (psi[idx + s] - psi[idx - s]) * (T)0.5;
     T dpos;
-    const T nn = (T)n * (T)n;
-    if (i == 0)          dpos = (psi[idx + s] - psi[idx]) * nn;
-    else if (i == n - 1) dpos = (psi[idx] - psi[idx - s]) * nn;
-    else                 dpos = (psi[idx + s] - psi[idx - s]) * (T)0.5 * nn;
+    if (!power) {
+        dpos = dpsi * ((T)n * (T)n);          // grad psi in cell units, divided by h
+    } else {
+        const T w = dpsi * (T)n;              // d psi / d x_a
+        dpos = copysign(pow_s<T>(fabs(w), (T)q), w) * (T)n;
+    }
     T pos = (T)i - dpos;
     pos = fmin(fmax(pos, (T)0), (T)(n - 1));
     return pos;
@@ -93,7 +115,7 @@ __global__ void pushforward_kernel(const T* __restrict__ psi, const T* __restric
         for (int a = 0; a < NDIM; ++a) {
             const int i = (int)(r % g.n[a]);
             r /= g.n[a];
-            pos[a] = map_pos(psi, idx, i, g.n[a], g.s[a]);
+            pos[a] = map_pos(psi, idx, i, g.n[a], g.s[a], g.power, g.q[a]);
         }
         deposit<T, NDIM>(rho, g, pos, m);
     }
@@ -134,7 +156,7 @@ __global__ void pushforward_batched_kernel(const PushArgs<T>* batch)
         for (int ax = 0; ax < NDIM; ++ax) {
             const int i = (int)(r % g.n[ax]);
             r /= g.n[ax];
-            pos[ax] = map_pos(a.psi, idx, i, g.n[ax], g.s[ax]);
+            pos[ax] = map_pos(a.psi, idx, i, g.n[ax], g.s[ax], g.power, g.q[ax]);
         }
         deposit<T, NDIM>(a.rho, g, pos, m);
     }
@@ -178,7 +200,7 @@ __global__ void map_kernel(const T* __restrict__ psi, T* __restrict__ out, GridD
         for (int a = 0; a < NDIM; ++a) {
             const int i = (int)(r % g.n[a]);
             r /= g.n[a];
-            const T pos = map_pos(psi, idx, i, g.n[a], g.s[a]);
+            const T pos = map_pos(psi, idx, i, g.n[a], g.s[a], g.power, g.q[a]);
             out[a * g.N + idx] = (pos + (T)0.5) / (T)g.n[a];
         }
     }
@@ -209,10 +231,10 @@ __global__ void interpolate_kernel(const T* __restrict__ map, const T* __restric
 
 template <typename T>
 bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho, const int* done,
-                              cudaStream_t st)
+                              cudaStream_t st, const double* p)
 {
     BFM_CUDA(cudaMemsetAsync(rho, 0, sizeof(T) * g.N, st));
-    const GridDev d = dev_grid(g);
+    const GridDev d = dev_grid(g, p);
     const int th = 256, bl = grid_blocks(g.N, th);
     if (g.ndim == 2) pushforward_kernel<T, 2><<<bl, th, 0, st>>>(psi, mu, rho, d, done);
     else             pushforward_kernel<T, 3><<<bl, th, 0, st>>>(psi, mu, rho, d, done);
@@ -221,9 +243,9 @@ bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho, 
 }
 
 template <typename T>
-bfm_status launch_map(const Grid& g, const T* psi, T* map, cudaStream_t st)
+bfm_status launch_map(const Grid& g, const T* psi, T* map, cudaStream_t st, const double* p)
 {
-    const GridDev d = dev_grid(g);
+    const GridDev d = dev_grid(g, p);
     const int th = 256, bl = grid_blocks(g.N, th);
     if (g.ndim == 2) map_kernel<T, 2><<<bl, th, 0, st>>>(psi, map, d);
     else             map_kernel<T, 3><<<bl, th, 0, st>>>(psi, map, d);
@@ -245,11 +267,11 @@ bfm_status launch_interpolate(const Grid& g, const T* map, const T* mu, double t
 }
 
 template bfm_status launch_pushforward<float>(const Grid&, const float*, const float*, float*,
-                                              const int*, cudaStream_t);
+                                              const int*, cudaStream_t, const double*);
 template bfm_status launch_pushforward<double>(const Grid&, const double*, const double*, double*,
-                                               const int*, cudaStream_t);
-template bfm_status launch_map<float>(const Grid&, const float*, float*, cudaStream_t);
-template bfm_status launch_map<double>(const Grid&, const double*, double*, cudaStream_t);
+                                               const int*, cudaStream_t, const double*);
+template bfm_status launch_map<float>(const Grid&, const float*, float*, cudaStream_t, const double*);
+template bfm_status launch_map<double>(const Grid&, const double*, double*, cudaStream_t, const double*);
 template bfm_status launch_interpolate<float>(const Grid&, const float*, const float*, double,
                                               float*, cudaStream_t);
 template bfm_status launch_interpolate<double>(const Grid&, const double*, const double*, double,

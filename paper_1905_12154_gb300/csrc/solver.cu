@@ -80,9 +80,12 @@ __global__ void scale_kernel(const T* __restrict__ in, T* __restrict__ out, long
 }
 
 __global__ void init_state_kernel(SolverState* st, double sigma0, double tol, int max_iter,
-                                  double b1, double b2, double a1, double a2, double smin)
+                                  double b1, double b2, double a1, double a2, double smin,
+                                  int power, double p0, double p1, double p2)
 {
     if (threadIdx.x != 0) return;
+    st->power = power;
+    st->cost_p[0] = p0; st->cost_p[1] = p1; st->cost_p[2] = p2;
     const double mxm = st->max_mu / st->mass_mu, mxn = st->max_nu / st->mass_nu;
     st->max_mu = mxm;
     st->max_nu = mxn;
@@ -241,8 +244,25 @@ static bfm_status transpose(const Grid& g, bool forward, const T* in, T* out, co
 template <typename T>
 static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_src, const T* w_out,
                                double* p_in, int* n_in, double* p_out, int* n_out, const int* done,
-                               cudaStream_t st, T* xt)
+                               cudaStream_t st, T* xt, const double* pc)
 {
+    if (pc) {
+        // separable power cost: every axis by the divide-and-conquer pass (columns
+        // as interleaved tiles; a tile is read whole before it is written)
+        for (int a = 0; a < g.ndim; ++a) {
+            const bool first = (a == 0), last = (a == g.ndim - 1);
+            int used = 0;
+            ProfScope ps(PK_CT0 + a, 1, st);
+            bfm_status s = launch_ct_power_pass<T>(g, a, pc[a], first ? src : out, out, first,
+                                                   first ? w_src : nullptr, first ? p_in : nullptr,
+                                                   last ? w_out : nullptr, last ? p_out : nullptr,
+                                                   done, kMaxPartials, st, &used);
+            if (s != BFM_OK) return s;
+            if (first) *n_in = used;
+            if (last) *n_out = used;
+        }
+        return BFM_OK;
+    }
     if (xt) {
         bfm_status s;
         {
@@ -340,7 +360,7 @@ constexpr int kFinThreads = 1024;
 
 template <typename T>
 bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
-                            Logs logs, cudaStream_t st)
+                            Logs logs, cudaStream_t st, const double* pc)
 {
     const double hd = 1.0 / (double)g.N;
     const int* done = &w->state->done;
@@ -358,7 +378,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     int ni = 0, no = 0, ng = 0;
     bfm_status s;
     T* xt = (T*)w->xt;
-    s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
+    s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -368,7 +388,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     }
     {
         ProfScope ps(PK_PUSH, 1, st);
-        s = launch_pushforward<T>(g, tmp, source, rho, done, st);
+        s = launch_pushforward<T>(g, tmp, source, rho, done, st, pc);
         if (s != BFM_OK) return s;
     }
     s = poisson_forward<T>(g, w->tabs, rho, target, rho, slot(w, 2), &ng, done, st, xt);
@@ -380,7 +400,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     }
     s = poisson_inverse<T>(g, w->tabs, rho, src, src, &w->state->sigma, done, st);
     if (s != BFM_OK) return s;
-    s = ct_with_dots<T>(g, src, dst, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
+    s = ct_with_dots<T>(g, src, dst, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -398,7 +418,8 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
 //   J(phi_{n+1/2}) - J(phi_n)), phi_{n+1} = psi_{n+1}^c, J(phi_{n+1}) =
 //   <phi_{n+1}, nu> + <psi_{n+1}, mu> logged (psi_{n+1}^{cc} = psi_{n+1}).
 template <typename T>
-static bfm_status ascent_step(const Grid& g, Workspace* w, T* phi, Logs logs, cudaStream_t st)
+static bfm_status ascent_step(const Grid& g, Workspace* w, T* phi, Logs logs, cudaStream_t st,
+                              const double* pc)
 {
     const double hd = 1.0 / (double)g.N;
     const int* done = &w->state->done;
@@ -411,7 +432,7 @@ static bfm_status ascent_step(const Grid& g, Workspace* w, T* phi, Logs logs, cu
     bfm_status s;
     {
         ProfScope ps(PK_PUSH, 1, st);
-        s = launch_pushforward<T>(g, tmp, mu, rho, done, st);
+        s = launch_pushforward<T>(g, tmp, mu, rho, done, st, pc);
         if (s != BFM_OK) return s;
     }
     s = poisson_forward<T>(g, w->tabs, rho, nu, rho, slot(w, 2), &ng, done, st, xt);
@@ -423,7 +444,7 @@ static bfm_status ascent_step(const Grid& g, Workspace* w, T* phi, Logs logs, cu
     }
     s = poisson_inverse<T>(g, w->tabs, rho, phi, phi, &w->state->sigma, done, st);
     if (s != BFM_OK) return s;
-    s = ct_with_dots<T>(g, phi, tmp, nu, mu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
+    s = ct_with_dots<T>(g, phi, tmp, nu, mu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -431,7 +452,7 @@ static bfm_status ascent_step(const Grid& g, Workspace* w, T* phi, Logs logs, cu
                                                         3, logs);
         BFM_LAUNCH_CHECK("finalize_dual_kernel");
     }
-    s = ct_with_dots<T>(g, tmp, phi, mu, nu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
+    s = ct_with_dots<T>(g, tmp, phi, mu, nu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -499,8 +520,10 @@ bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int ma
     scale_kernel<T><<<nb, th, 0, st>>>(mu, (T*)w.mu_n, g.N, w.state, 0);
     scale_kernel<T><<<nb, th, 0, st>>>(nu, (T*)w.nu_n, g.N, w.state, 1);
     BFM_LAUNCH_CHECK("scale_kernel");
+    const double* pc = cost_exponents(&o);
     init_state_kernel<<<1, 1, 0, st>>>(w.state, o.sigma0, tol, max_iter, o.beta1, o.beta2,
-                                       o.alpha1, o.alpha2, o.sigma_min);
+                                       o.alpha1, o.alpha2, o.sigma_min, pc ? 1 : 0,
+                                       o.cost_p[0], o.cost_p[1], o.cost_p[2]);
     BFM_LAUNCH_CHECK("init_state_kernel");
     s = fill_tables<T>(g, &w, st); if (s != BFM_OK) return s;
     // ||nu - 1||^2_{H^-1}: the mean of nu/mass is 1 and the zero mode is dropped
@@ -518,7 +541,7 @@ bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int ma
         // the ascent keeps psi_n = phi_n^c in tmp; measure J(phi_0)
         int ni = 0, no = 0;
         s = ct_with_dots<T>(g, phi, (T*)w.tmp, (const T*)w.nu_n, (const T*)w.mu_n, slot(&w, 0), &ni,
-                            slot(&w, 1), &no, &w.state->done, st, (T*)w.xt);
+                            slot(&w, 1), &no, &w.state->done, st, (T*)w.xt, pc);
         if (s != BFM_OK) return s;
         finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w.state, slot(&w, 0), ni, slot(&w, 1), no,
                                                         1.0 / (double)g.N, 0, logs);
@@ -530,21 +553,22 @@ bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int ma
 // Enqueue `iters` back-and-forth iterations; no host synchronisation.
 template <typename T>
 static bfm_status iterate_impl(const Grid& g, int max_iter, int iters, int method,
-                               unsigned char* wsp, cudaStream_t st, T* phi, T* psi)
+                               const double* pc, unsigned char* wsp, cudaStream_t st, T* phi,
+                               T* psi)
 {
     Workspace w;
     carve(g, sizeof(T), max_iter, wsp, &w, true);
     Logs logs = logs_of(&w, max_iter);
     if (method == BFM_GRADIENT_ASCENT) {
         for (int c = 0; c < iters; ++c) {
-            bfm_status s = ascent_step<T>(g, &w, phi, logs, st);
+            bfm_status s = ascent_step<T>(g, &w, phi, logs, st, pc);
             if (s != BFM_OK) return s;
         }
         return BFM_OK;
     }
     for (int c = 0; c < iters; ++c) {
-        bfm_status s = half_step<T>(g, &w, true, phi, psi, logs, st); if (s != BFM_OK) return s;
-        s = half_step<T>(g, &w, false, phi, psi, logs, st); if (s != BFM_OK) return s;
+        bfm_status s = half_step<T>(g, &w, true, phi, psi, logs, st, pc); if (s != BFM_OK) return s;
+        s = half_step<T>(g, &w, false, phi, psi, logs, st, pc); if (s != BFM_OK) return s;
     }
     return BFM_OK;
 }
@@ -571,9 +595,14 @@ bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, cudaStre
     Logs logs = logs_of(&w, max_iter);
     T* phi = (T*)out->phi;
     T* psi = (T*)out->psi;
+    // the cost the solve was started with (finish synchronises anyway)
+    SolverState hs0;
+    BFM_CUDA(cudaMemcpyAsync(&hs0, w.state, sizeof(hs0), cudaMemcpyDeviceToHost, st));
+    BFM_CUDA(cudaStreamSynchronize(st));
+    const double* pc = hs0.power ? hs0.cost_p : nullptr;
     stop_now_kernel<<<1, 32, 0, st>>>(w.state);
     BFM_LAUNCH_CHECK("stop_now_kernel");
-    bfm_status s = half_step<T>(g, &w, true, phi, psi, logs, st);
+    bfm_status s = half_step<T>(g, &w, true, phi, psi, logs, st, pc);
     if (s != BFM_OK) return s;
     SolverState hs;
     BFM_CUDA(cudaMemcpyAsync(&hs, w.state, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -583,7 +612,7 @@ bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, cudaStre
         return BFM_ERR_NONFINITE;
     }
     BFM_CUDA(cudaMemcpyAsync(psi, w.tmp, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, st));
-    if (out->map) { s = launch_map<T>(g, psi, (T*)out->map, st); if (s != BFM_OK) return s; }
+    if (out->map) { s = launch_map<T>(g, psi, (T*)out->map, st, pc); if (s != BFM_OK) return s; }
     const int nlog = hs.iter + 1;
     if (out->dual) BFM_CUDA(cudaMemcpyAsync(out->dual, logs.dual, sizeof(double) * nlog, cudaMemcpyDeviceToHost, st));
     if (out->resid) BFM_CUDA(cudaMemcpyAsync(out->resid, logs.resid, sizeof(double) * nlog, cudaMemcpyDeviceToHost, st));
@@ -638,6 +667,35 @@ extern "C" size_t bfm_poisson_workspace_bytes(const bfm_grid* grid, bfm_precisio
     return poisson_bytes(g, elem_bytes(prec));
 }
 
+const double* bfm::cost_exponents(const bfm_options* o)
+{
+    return (o && o->cost_p[0] > 0.0) ? o->cost_p : nullptr;
+}
+
+static bool exponents_ok(const double* p, int ndim)
+{
+    for (int a = 0; a < ndim; ++a)
+        if (!(p[a] > 1.0 && p[a] <= 16.0)) return false;
+    return true;
+}
+
+// BFM_COST_QUADRATIC takes cost_p all zero; BFM_COST_POWER takes 1 < p_a <= 16
+static bfm_status check_cost(bfm_cost cost, const bfm_options& o, const Grid& g)
+{
+    if (cost == BFM_COST_QUADRATIC) {
+        if (o.cost_p[0] != 0.0 || o.cost_p[1] != 0.0 || o.cost_p[2] != 0.0) {
+            set_last_error("cost_p must be zero for the quadratic cost");
+            return BFM_ERR_INVALID_ARG;
+        }
+        return BFM_OK;
+    }
+    if (!exponents_ok(o.cost_p, g.ndim)) {
+        set_last_error("the power cost needs 1 < cost_p[a] <= 16 on every axis");
+        return BFM_ERR_INVALID_ARG;
+    }
+    return BFM_OK;
+}
+
 static bfm_status check_common(const bfm_grid* grid, bfm_precision prec, Grid* g)
 {
     if (prec != BFM_FP32 && prec != BFM_FP64) return BFM_ERR_INVALID_ARG;
@@ -671,7 +729,10 @@ extern "C" bfm_status bfm_solver_init(const void* mu, const void* nu, const bfm_
     Grid g;
     bfm_status s = check_solver_args(grid, prec, max_iter, workspace, workspace_bytes, &g);
     if (s != BFM_OK) return s;
-    if (cost != BFM_COST_QUADRATIC) { set_last_error("only the quadratic cost is implemented"); return BFM_ERR_UNSUPPORTED; }
+    if (cost != BFM_COST_QUADRATIC && cost != BFM_COST_POWER) {
+        set_last_error("unknown cost");
+        return BFM_ERR_UNSUPPORTED;
+    }
     if (!mu || !nu || !phi || !psi || !(tol >= 0.0)) {
         set_last_error("null pointer or negative tolerance");
         return BFM_ERR_INVALID_ARG;
@@ -688,6 +749,8 @@ extern "C" bfm_status bfm_solver_init(const void* mu, const void* nu, const bfm_
         set_last_error("unknown method");
         return BFM_ERR_INVALID_ARG;
     }
+    s = check_cost(cost, o, g);
+    if (s != BFM_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* wsp = (unsigned char*)workspace;
     if (prec == BFM_FP32)
@@ -710,11 +773,14 @@ extern "C" bfm_status bfm_solver_iterate(const bfm_grid* grid, bfm_precision pre
         set_last_error("unknown method");
         return BFM_ERR_INVALID_ARG;
     }
+    const double* pc = cost_exponents(opt);
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* wsp = (unsigned char*)workspace;
     if (prec == BFM_FP32)
-        return iterate_impl<float>(g, max_iter, iterations, method, wsp, st, (float*)phi, (float*)psi);
-    return iterate_impl<double>(g, max_iter, iterations, method, wsp, st, (double*)phi, (double*)psi);
+        return iterate_impl<float>(g, max_iter, iterations, method, pc, wsp, st, (float*)phi,
+                                   (float*)psi);
+    return iterate_impl<double>(g, max_iter, iterations, method, pc, wsp, st, (double*)phi,
+                                (double*)psi);
 }
 
 extern "C" bfm_status bfm_solver_finish(const bfm_grid* grid, bfm_precision prec, int max_iter,
@@ -870,6 +936,47 @@ extern "C" bfm_status bfm_ctransform(const void* phi, void* out, const bfm_grid*
     }
     BFM_LAUNCH_CHECK("ct_pass_kernel");
     return BFM_OK;
+}
+
+extern "C" bfm_status bfm_ctransform_power(const void* phi, void* out, const bfm_grid* grid,
+                                           bfm_precision prec, const double* p, void* stream)
+{
+    Grid g;
+    bfm_status s = check_common(grid, prec, &g);
+    if (s != BFM_OK) return s;
+    if (!phi || !out || !p || !exponents_ok(p, g.ndim)) {
+        set_last_error("null pointer or exponent outside (1, 16]");
+        return BFM_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int a = 0; a < g.ndim; ++a) {
+        if (prec == BFM_FP32)
+            s = launch_ct_power_pass<float>(g, a, p[a], a == 0 ? (const float*)phi : (const float*)out,
+                                            (float*)out, a == 0, nullptr, nullptr, nullptr, nullptr,
+                                            nullptr, 0, st, nullptr);
+        else
+            s = launch_ct_power_pass<double>(g, a, p[a], a == 0 ? (const double*)phi : (const double*)out,
+                                             (double*)out, a == 0, nullptr, nullptr, nullptr, nullptr,
+                                             nullptr, 0, st, nullptr);
+        if (s != BFM_OK) return s;
+    }
+    BFM_LAUNCH_CHECK("ct_power_kernel");
+    return BFM_OK;
+}
+
+extern "C" bfm_status bfm_map_power(const void* psi, void* map, const bfm_grid* grid,
+                                    bfm_precision prec, const double* p, void* stream)
+{
+    Grid g;
+    bfm_status s = check_common(grid, prec, &g);
+    if (s != BFM_OK) return s;
+    if (!psi || !map || !p || !exponents_ok(p, g.ndim)) {
+        set_last_error("null pointer or exponent outside (1, 16]");
+        return BFM_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == BFM_FP32) return launch_map<float>(g, (const float*)psi, (float*)map, st, p);
+    return launch_map<double>(g, (const double*)psi, (double*)map, st, p);
 }
 
 template <typename T>

@@ -23,7 +23,8 @@ struct SolverState {
     int done;
     int converged;
     int nonfinite;
-    int pad;
+    int power;                // separable power cost with exponents cost_p
+    double cost_p[3];
 };
 
 struct Logs {
@@ -64,6 +65,8 @@ bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int ma
 template <typename T>
 bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, cudaStream_t st,
                        bfm_result* out);
+// exponents of the solve's cost from its options: NULL for the quadratic cost
+const double* cost_exponents(const bfm_options* o);
 
 // ---------------------------------------------------------------------------
 // device-side scalar logic of one half step (run by one thread)
