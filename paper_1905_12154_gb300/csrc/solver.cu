@@ -573,6 +573,79 @@ static bfm_status iterate_impl(const Grid& g, int max_iter, int iters, int metho
     return BFM_OK;
 }
 
+// A chunk of iterations captured once as a CUDA graph and replayed on a
+// private non-blocking stream, which events order after the caller's stream
+// on entry and the caller's stream after it on exit (nothing blocks).  The
+// graph lives for one C-ABI call: the host keeps nothing between calls.
+// Replays skip the per-kernel launch work of the host and the gaps it leaves.
+struct ChunkGraph {
+    cudaStream_t ps = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~ChunkGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);    // freed when in-flight replays finish
+        if (graph) cudaGraphDestroy(graph);
+        if (ev) cudaEventDestroy(ev);
+        if (ps) cudaStreamDestroy(ps);
+    }
+    bfm_status begin(cudaStream_t user)
+    {
+        BFM_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+        BFM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        BFM_CUDA(cudaEventRecord(ev, user));
+        BFM_CUDA(cudaStreamWaitEvent(ps, ev, 0));
+        return BFM_OK;
+    }
+    template <typename F>
+    bfm_status capture(F enqueue)
+    {
+        BFM_CUDA(cudaStreamBeginCapture(ps, cudaStreamCaptureModeRelaxed));
+        const bfm_status s = enqueue(ps);
+        const cudaError_t e = cudaStreamEndCapture(ps, &graph);     // always ends the capture
+        if (s != BFM_OK) return s;
+        if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+        BFM_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        return BFM_OK;
+    }
+    bfm_status launch() { BFM_CUDA(cudaGraphLaunch(exec, ps)); return BFM_OK; }
+    bfm_status end(cudaStream_t user)
+    {
+        BFM_CUDA(cudaEventRecord(ev, ps));
+        BFM_CUDA(cudaStreamWaitEvent(user, ev, 0));
+        return BFM_OK;
+    }
+};
+
+constexpr int kGraphChunk = 4;       // iterations per captured graph
+
+// `iters` iterations: replays of a captured chunk when there are enough of
+// them and the per-launch profiler is off (its events must be recorded per
+// launch), else plain launches on `user`.
+template <typename T>
+static bfm_status iterate_chunked(const Grid& g, int max_iter, int iters, int method,
+                                  const double* pc, unsigned char* wsp, cudaStream_t user, T* phi,
+                                  T* psi)
+{
+    if (g_prof.on || iters < 2 * kGraphChunk)
+        return iterate_impl<T>(g, max_iter, iters, method, pc, wsp, user, phi, psi);
+    ChunkGraph cg;
+    bfm_status s = cg.begin(user);
+    if (s != BFM_OK) return s;
+    s = cg.capture([&](cudaStream_t st) {
+        return iterate_impl<T>(g, max_iter, kGraphChunk, method, pc, wsp, st, phi, psi);
+    });
+    if (s != BFM_OK) return s;
+    for (int r = 0; r < iters / kGraphChunk; ++r) {
+        s = cg.launch();
+        if (s != BFM_OK) return s;
+    }
+    s = iterate_impl<T>(g, max_iter, iters % kGraphChunk, method, pc, wsp, cg.ps, phi, psi);
+    if (s != BFM_OK) return s;
+    return cg.end(user);
+}
+
 static bfm_status read_done(const Grid& g, int eb, int max_iter, unsigned char* wsp,
                             cudaStream_t st, int* done)
 {
@@ -777,10 +850,10 @@ extern "C" bfm_status bfm_solver_iterate(const bfm_grid* grid, bfm_precision pre
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* wsp = (unsigned char*)workspace;
     if (prec == BFM_FP32)
-        return iterate_impl<float>(g, max_iter, iterations, method, pc, wsp, st, (float*)phi,
-                                   (float*)psi);
-    return iterate_impl<double>(g, max_iter, iterations, method, pc, wsp, st, (double*)phi,
-                                (double*)psi);
+        return iterate_chunked<float>(g, max_iter, iterations, method, pc, wsp, st, (float*)phi,
+                                      (float*)psi);
+    return iterate_chunked<double>(g, max_iter, iterations, method, pc, wsp, st, (double*)phi,
+                                   (double*)psi);
 }
 
 extern "C" bfm_status bfm_solver_finish(const bfm_grid* grid, bfm_precision prec, int max_iter,
@@ -809,6 +882,35 @@ extern "C" bfm_status bfm_solve(const void* mu, const void* nu, const bfm_grid* 
     Grid g;
     make_grid(grid, &g);
     const int poll = (opt && opt->poll_every > 0) ? opt->poll_every : 4;
+    if (!g_prof.on) {
+        // one captured chunk of `poll` iterations, replayed between polls
+        const int method = opt ? opt->method : BFM_BACK_AND_FORTH;
+        const double* pc = cost_exponents(opt);
+        unsigned char* wsp = (unsigned char*)workspace;
+        cudaStream_t user = (cudaStream_t)stream;
+        ChunkGraph cg;
+        s = cg.begin(user);
+        if (s != BFM_OK) return s;
+        s = cg.capture([&](cudaStream_t st) {
+            if (prec == BFM_FP32)
+                return iterate_impl<float>(g, max_iter, poll, method, pc, wsp, st,
+                                           (float*)out->phi, (float*)out->psi);
+            return iterate_impl<double>(g, max_iter, poll, method, pc, wsp, st,
+                                        (double*)out->phi, (double*)out->psi);
+        });
+        if (s != BFM_OK) return s;
+        for (int enq = 0; enq <= max_iter; enq += poll) {
+            s = cg.launch();
+            if (s != BFM_OK) return s;
+            int done = 0;
+            s = read_done(g, elem_bytes(prec), max_iter, wsp, cg.ps, &done);
+            if (s != BFM_OK) return s;
+            if (done) break;
+        }
+        s = cg.end(user);
+        if (s != BFM_OK) return s;
+        return bfm_solver_finish(grid, prec, max_iter, workspace, workspace_bytes, stream, out);
+    }
     int enq = 0;
     while (enq <= max_iter) {
         const int chunk = (max_iter + 1 - enq) < poll ? (max_iter + 1 - enq) : poll;
