@@ -684,7 +684,12 @@ bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, cudaStre
         set_last_error("a reduction produced a non-finite value");
         return BFM_ERR_NONFINITE;
     }
-    BFM_CUDA(cudaMemcpyAsync(psi, w.tmp, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, st));
+    // psi = phi_n^c formed afresh from the final phi (no done flag: it runs
+    // even when the loop stopped inside a half step)
+    int nd0 = 0, nd1 = 0;
+    s = ct_with_dots<T>(g, phi, psi, nullptr, nullptr, nullptr, &nd0, nullptr, &nd1, nullptr, st,
+                        (T*)w.xt, pc);
+    if (s != BFM_OK) return s;
     if (out->map) { s = launch_map<T>(g, psi, (T*)out->map, st, pc); if (s != BFM_OK) return s; }
     const int nlog = hs.iter + 1;
     if (out->dual) BFM_CUDA(cudaMemcpyAsync(out->dual, logs.dual, sizeof(double) * nlog, cudaMemcpyDeviceToHost, st));
