@@ -501,7 +501,7 @@ __device__ void stockham_fft(float2* z, int n, int t, int T, bool active, const 
 }
 
 template <int MODE, bool CONTIG, bool BATCHED>
-__global__ void __launch_bounds__(512, 1) dct_fast_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
+__global__ void __launch_bounds__(256, 2) dct_fast_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
 {
     using C = float2;
     using T = float;
@@ -856,7 +856,9 @@ DctPlan plan_dct_pass(const Grid& g, int axis, int elem_bytes)
     int G, max_threads;
     if (p.fast) {
         G = n / 16;                                   // 16 complex values per thread per pass
-        max_threads = 512;                            // up to 128 registers per thread
+        // up to 128 registers per thread: one line pair per CTA and two CTAs
+        // per SM, so one CTA's loads and stores overlap the other's FFT
+        max_threads = 256;
         p.LDZ = n + n / 16 + 1;                       // one pad element per 16
     } else {
         G = n / 8;
