@@ -475,7 +475,7 @@ __device__ __forceinline__ void pass_write(float2* z, int Ns, int t, int T, cons
 
 // One FFT of every pair held by the CTA (all threads take part: barriers).
 template <int SIGN>
-__device__ void stockham_fft(float2* z, int n, int t, int T, bool active, const float2* ptw,
+__device__ __forceinline__ void stockham_fft(float2* z, int n, int t, int T, bool active, const float2* ptw,
                              int nst, const int* rad)
 {
     float2 v[16];
@@ -498,6 +498,16 @@ __device__ void stockham_fft(float2* z, int n, int t, int T, bool active, const 
         __syncthreads();
         Ns *= R;
     }
+}
+
+// The MID pass runs a forward and an inverse FFT in one kernel; inlined
+// together they exceed 128 registers and spill, so there each FFT is a call
+// with its own register allocation.
+template <int SIGN>
+__device__ __noinline__ void stockham_fft_call(float2* z, int n, int t, int T, bool active,
+                                               const float2* ptw, int nst, const int* rad)
+{
+    stockham_fft<SIGN>(z, n, t, T, active, ptw, nst, rad);
 }
 
 template <int MODE, bool CONTIG, bool BATCHED>
@@ -573,7 +583,8 @@ __global__ void __launch_bounds__(256, 2) dct_fast_kernel(DctArgs<float> a0, con
         }
         __syncthreads();
         if (MODE != DCT_INV) {
-            stockham_fft<-1>(z, n, t, G, active, a.ptw, a.fnst, a.frad);
+            if (MODE == DCT_MID) stockham_fft_call<-1>(z, n, t, G, active, a.ptw, a.fnst, a.frad);
+            else stockham_fft<-1>(z, n, t, G, active, a.ptw, a.fnst, a.frad);
             if (active) {
                 for (int k = t; k <= n / 2; k += G) {
                     const int km = (n - k) % n;
@@ -648,7 +659,8 @@ __global__ void __launch_bounds__(256, 2) dct_fast_kernel(DctArgs<float> a0, con
                 }
             }
             __syncthreads();
-            stockham_fft<+1>(z, n, t, G, active, a.ptw, a.fnst, a.frad);
+            if (MODE == DCT_MID) stockham_fft_call<+1>(z, n, t, G, active, a.ptw, a.fnst, a.frad);
+            else stockham_fft<+1>(z, n, t, G, active, a.ptw, a.fnst, a.frad);
         }
         // ---- store (the potential update reads its U values first) ------------------
         {
