@@ -43,6 +43,8 @@ template <typename T> __device__ __forceinline__ T pow_s(T x, T y);
 template <> __device__ __forceinline__ float pow_s<float>(float x, float y) { return powf(x, y); }
 template <> __device__ __forceinline__ double pow_s<double>(double x, double y) { return pow(x, y); }
 
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 static int grid_blocks(long long N, int threads)
 {
     long long b = (N + threads - 1) / threads;
@@ -52,15 +54,15 @@ static int grid_blocks(long long N, int threads)
     return (int)b;
 }
 
-// position of T(x) along one axis, in cell-index units, clamped to [0, n-1]
+// position of T(x) along one axis, in cell-index units, clamped to [0, n-1],
+// from psi at the cell (pc) and its neighbours before (pm) and after (pp)
 template <typename T>
-__device__ __forceinline__ T map_pos(const T* psi, long long idx, int i, int n, long long s,
-                                     int power, double q)
+__device__ __forceinline__ T axis_pos(T pm, T pc, T pp, int i, int n, int power, double q)
 {
     T dpsi;                                   // psi difference per cell
-    if (i == 0)          dpsi = psi[idx + s] - psi[idx];
-    else if (i == n - 1) dpsi = psi[idx] - psi[idx - s];
-    else                 dpsi = (psi[idx + s] - psi[idx - s]) * (T)0.5;
+    if (i == 0)          dpsi = pp - pc;
+    else if (i == n - 1) dpsi = pc - pm;
+    else                 dpsi = (pp - pm) * (T)0.5;
     T dpos;
     if (!power) {
         dpos = dpsi * ((T)n * (T)n);          // grad psi in cell units, divided by h
@@ -71,6 +73,15 @@ __device__ __forceinline__ T map_pos(const T* psi, long long idx, int i, int n, 
     T pos = (T)i - dpos;
     pos = fmin(fmax(pos, (T)0), (T)(n - 1));
     return pos;
+}
+
+template <typename T>
+__device__ __forceinline__ T map_pos(const T* psi, long long idx, int i, int n, long long s,
+                                     int power, double q)
+{
+    const T pm = i > 0 ? psi[idx - s] : (T)0;
+    const T pp = i < n - 1 ? psi[idx + s] : (T)0;
+    return axis_pos(pm, psi[idx], pp, i, n, power, q);
 }
 
 template <typename T, int NDIM>
@@ -118,6 +129,126 @@ __global__ void pushforward_kernel(const T* __restrict__ psi, const T* __restric
             pos[a] = map_pos(psi, idx, i, g.n[a], g.s[a], g.power, g.q[a]);
         }
         deposit<T, NDIM>(rho, g, pos, m);
+    }
+}
+
+// The pushforward along rows: one 16-byte vector of cells per thread (4 FP32
+// or 2 FP64 cells), a CTA segment of 256 vectors of one line along axis 0 per
+// step, so the row and column indices cost one division per segment instead
+// of per cell.  FP32 deposits go out as vector reductions: the two cells
+// (c, c + 1) of a line that a bilinear deposit touches are one 8-byte red
+// when c is even, one 16-byte red with zero ends when c = 1 mod 4, else two
+// scalar reds.  Needs n0 % 4 == 0 and 16-byte aligned fields.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int V = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int V = 2; };
+
+template <typename T>
+__device__ __forceinline__ void unpack(const typename Vec16<T>::type& v, T* o);
+template <> __device__ __forceinline__ void unpack<float>(const float4& v, float* o)
+{ o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+template <> __device__ __forceinline__ void unpack<double>(const double2& v, double* o)
+{ o[0] = v.x; o[1] = v.y; }
+
+// rho[q] += a, rho[q + 1] += b
+__device__ __forceinline__ void red_pair(float* rho, long long q, float a, float b)
+{
+    const int r = (int)(q & 3);
+    if ((r & 1) == 0) {
+        atomicAdd(reinterpret_cast<float2*>(rho + q), make_float2(a, b));
+    } else if (r == 1) {
+        atomicAdd(reinterpret_cast<float4*>(rho + q - 1), make_float4(0.f, a, b, 0.f));
+    } else {
+        atomicAdd(rho + q, a);
+        atomicAdd(rho + q + 1, b);
+    }
+}
+__device__ __forceinline__ void red_pair(double* rho, long long q, double a, double b)
+{
+    if (a != 0.0) atomicAdd(rho + q, a);
+    if (b != 0.0) atomicAdd(rho + q + 1, b);
+}
+
+template <typename T, int NDIM>
+__device__ __forceinline__ void deposit_rows(T* rho, const GridDev& g, const T* pos, T m)
+{
+    int i0[3];
+    T w1[3];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        int c = (int)floor(pos[a]);
+        if (c > g.n[a] - 2) c = g.n[a] - 2;
+        if (c < 0) c = 0;
+        i0[a] = c;
+        w1[a] = pos[a] - (T)c;
+    }
+#pragma unroll
+    for (int c = 0; c < (1 << (NDIM - 1)); ++c) {
+        T w = m;
+        long long q = i0[0];
+#pragma unroll
+        for (int a = 1; a < NDIM; ++a) {
+            const int up = (c >> (a - 1)) & 1;
+            w *= up ? w1[a] : ((T)1 - w1[a]);
+            q += (long long)(i0[a] + up) * g.s[a];
+        }
+        red_pair(rho, q, w * ((T)1 - w1[0]), w * w1[0]);
+    }
+}
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restrict__ psi,
+                                                               const T* __restrict__ mu,
+                                                               T* __restrict__ rho, GridDev g,
+                                                               int segs, const int* done)
+{
+    if (done && *done) return;
+    using VT = typename Vec16<T>::type;
+    constexpr int V = Vec16<T>::V;
+    const int n0 = g.n[0];
+    const long long rows = g.N / n0;
+    const long long items = rows * segs;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const long long row = it / segs;
+        const int x0 = ((int)(it - row * segs) * blockDim.x + threadIdx.x) * V;
+        if (x0 >= n0) continue;
+        const long long base = row * n0 + x0;
+        T m[V];
+        unpack<T>(*reinterpret_cast<const VT*>(mu + base), m);
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < V; ++k) any |= (m[k] != (T)0);
+        if (!any) continue;
+        T c[V + 2];                                   // psi at x0 - 1 .. x0 + V along the row
+        unpack<T>(*reinterpret_cast<const VT*>(psi + base), c + 1);
+        c[0] = x0 > 0 ? psi[base - 1] : (T)0;
+        c[V + 1] = x0 + V < n0 ? psi[base + V] : (T)0;
+        int ia[3] = {0, 0, 0};
+        T lo[NDIM - 1][V], hi[NDIM - 1][V];       // neighbours along axes 1.. (unused at a face)
+#pragma unroll
+        for (int a = 0; a < NDIM - 1; ++a)
+#pragma unroll
+            for (int k = 0; k < V; ++k) lo[a][k] = hi[a][k] = c[k + 1];
+        {
+            long long r = row;
+#pragma unroll
+            for (int a = 1; a < NDIM; ++a) {
+                ia[a] = (int)(r % g.n[a]);
+                r /= g.n[a];
+                if (ia[a] > 0) unpack<T>(*reinterpret_cast<const VT*>(psi + base - g.s[a]), lo[a - 1]);
+                if (ia[a] < g.n[a] - 1) unpack<T>(*reinterpret_cast<const VT*>(psi + base + g.s[a]), hi[a - 1]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            if (m[k] == (T)0) continue;
+            T pos[3];
+            pos[0] = axis_pos(c[k], c[k + 1], c[k + 2], x0 + k, n0, g.power, g.q[0]);
+#pragma unroll
+            for (int a = 1; a < NDIM; ++a)
+                pos[a] = axis_pos(lo[a - 1][k], c[k + 1], hi[a - 1][k], ia[a], g.n[a], g.power, g.q[a]);
+            deposit_rows<T, NDIM>(rho, g, pos, m[k]);
+        }
     }
 }
 
@@ -236,6 +367,18 @@ bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho, 
     BFM_CUDA(cudaMemsetAsync(rho, 0, sizeof(T) * g.N, st));
     const GridDev d = dev_grid(g, p);
     const int th = 256, bl = grid_blocks(g.N, th);
+    const bool rows = g.n[0] % 4 == 0 && aligned16(psi) && aligned16(mu) && aligned16(rho);
+    if (rows) {
+        constexpr int V = Vec16<T>::V;
+        const int segs = (g.n[0] / V + th - 1) / th;
+        long long items = (g.N / g.n[0]) * segs;
+        const long long cap = (long long)num_sms() * 8;
+        const int blr = (int)(items < cap ? items : cap);
+        if (g.ndim == 2) pushforward_rows_kernel<T, 2><<<blr, th, 0, st>>>(psi, mu, rho, d, segs, done);
+        else             pushforward_rows_kernel<T, 3><<<blr, th, 0, st>>>(psi, mu, rho, d, segs, done);
+        BFM_LAUNCH_CHECK("pushforward_rows_kernel");
+        return BFM_OK;
+    }
     if (g.ndim == 2) pushforward_kernel<T, 2><<<bl, th, 0, st>>>(psi, mu, rho, d, done);
     else             pushforward_kernel<T, 3><<<bl, th, 0, st>>>(psi, mu, rho, d, done);
     BFM_LAUNCH_CHECK("pushforward_kernel");
