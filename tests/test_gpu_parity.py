@@ -140,6 +140,21 @@ def test_pushforward_fp32(B):
     assert np.max(np.abs(rho - want)) <= 2e-5 * np.max(want)
 
 
+@pytest.mark.parametrize("shape", [(1028, 6), (64, 40), (12, 10, 8), (6, 9), (8, 6, 5)], ids=str)
+@pytest.mark.parametrize("amp", [0.1, 2.0])
+def test_pushforward_fp32_shapes(B, shape, amp):
+    """Lines of 4k cells take the vector row kernel (one 16-byte vector per
+    thread, ragged last segment at 1028), others the per-cell kernel; amp 2
+    sends much of the mass past the box and onto its faces."""
+    mu = si.normalise(np.abs(si.random_field(shape, 12)) * (si.random_field(shape, 13) > -0.3))
+    mu = mu.astype(np.float32)
+    psi = (amp * si.smooth_potential(tuple(reversed(shape)), 14, 0.1)).astype(np.float32)
+    rho = host(B.bfm_pushforward(dev(psi, torch.float32), dev(mu, torch.float32)))
+    want = oracle.pushforward(psi.astype(np.float64), mu.astype(np.float64))
+    assert np.max(np.abs(rho - want)) <= 2e-5 * np.max(want)
+    assert abs(rho.sum() - mu.astype(np.float64).sum()) <= 1e-5 * mu.sum()
+
+
 def test_interpolate(B):
     n = 64
     mu, nu = si.translated_discs(n)
@@ -338,6 +353,41 @@ def test_long_columns_take_transposed_sweeps(B, shape, dt):
     assert prof["transpose"][1] == 12
     assert prof["ct_pass_axis0"][1] == prof["ct_pass_axis1"][1] == 4
     assert prof["dct_fwd"][1] == prof["dct_mid"][1] == prof["dct_inv"][1] == 2
+    assert prof["_dropped"][1] == 0
+
+
+# FP32 grids with long columns and long rows: both sweeps of every c-transform
+# take the row kernel (the axis-1 sweep on the transposed copy); 324 columns
+# leave a partial last round of 8-line CTAs in the sweep of the copy, and
+# rows of 288 or 324 cells take 16 cells per thread and 16 lines per CTA.
+# psi = phi^c of the returned phi is checked cell by cell.
+
+@pytest.mark.parametrize("shape", [(288, 2048), (324, 2048)], ids=str)
+def test_solve_long_rows_and_columns_fp32(B, shape):
+    mu, nu = long_column_pair(shape, 44)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=6)
+    r = B.bfm_solve(dev(mu, torch.float32), dev(nu, torch.float32), tol=0.0, max_iter=6)
+    assert r["iters"] == 6
+    assert abs(r["w2sq"] - ref["w2sq"]) / ref["w2sq"] < 1e-5
+    assert np.max(np.abs(r["resid"] - ref["resid"])) < 1e-3
+    phi = host(r["phi"])
+    want = oracle.ctransform(phi, "linear")
+    scale = 1.0 + np.max(np.abs(phi))
+    assert np.max(np.abs(host(r["psi"]) - want)) <= 4 * np.finfo(np.float32).eps * scale
+
+
+@pytest.mark.parametrize("shape,transposes", [((288, 2048), 12), ((2048, 2048), 12), ((486, 2048), 12),
+                                              ((2048, 288), 0)], ids=str)
+def test_transposes_follow_column_length(B, shape, transposes):
+    """FP32 columns of 2048 cells are swept as rows of a transposed copy
+    whatever the row length; short columns (2048 x 288) use column tiles."""
+    mu, nu = long_column_pair(shape, 45)
+    s = B.BfmSolver(dev(mu, torch.float32), dev(nu, torch.float32), tol=0.0, max_iter=10)
+    B.bfm_profile_begin(200)
+    s.iterate(1)
+    prof = B.bfm_profile_end()
+    assert prof["transpose"][1] == transposes
+    assert prof["ct_pass_axis0"][1] == prof["ct_pass_axis1"][1] == 4
     assert prof["_dropped"][1] == 0
 
 
