@@ -163,38 +163,66 @@ __device__ __forceinline__ void red_pair(float* rho, long long q, float a, float
         atomicAdd(rho + q + 1, b);
     }
 }
+
 __device__ __forceinline__ void red_pair(double* rho, long long q, double a, double b)
 {
     if (a != 0.0) atomicAdd(rho + q, a);
     if (b != 0.0) atomicAdd(rho + q + 1, b);
 }
 
+// Deposits of a thread's consecutive cells: cells whose multilinear stencils
+// coincide (a map that contracts along the row) are summed in registers and
+// sent as one set of reductions.
 template <typename T, int NDIM>
-__device__ __forceinline__ void deposit_rows(T* rho, const GridDev& g, const T* pos, T m)
-{
-    int i0[3];
-    T w1[3];
+struct StencilAcc {
+    static constexpr int C = 1 << (NDIM - 1);     // lines of the stencil across axes 1..
+    long long q0 = -1;                            // offset of the stencil's first cell
+    T a[C], b[C];                                 // weights at q_c and q_c + 1
+    __device__ __forceinline__ void flush(T* rho, const GridDev& g)
+    {
+        if (q0 < 0) return;
 #pragma unroll
-    for (int a = 0; a < NDIM; ++a) {
-        int c = (int)floor(pos[a]);
-        if (c > g.n[a] - 2) c = g.n[a] - 2;
-        if (c < 0) c = 0;
-        i0[a] = c;
-        w1[a] = pos[a] - (T)c;
+        for (int c = 0; c < C; ++c) {
+            long long q = q0;
+#pragma unroll
+            for (int ax = 1; ax < NDIM; ++ax) q += ((c >> (ax - 1)) & 1) * g.s[ax];
+            red_pair(rho, q, a[c], b[c]);
+        }
     }
+    __device__ __forceinline__ void add(T* rho, const GridDev& g, const T* pos, T m)
+    {
+        int i0[3];
+        T w1[3];
 #pragma unroll
-    for (int c = 0; c < (1 << (NDIM - 1)); ++c) {
-        T w = m;
+        for (int ax = 0; ax < NDIM; ++ax) {
+            int c = (int)floor(pos[ax]);
+            if (c > g.n[ax] - 2) c = g.n[ax] - 2;
+            if (c < 0) c = 0;
+            i0[ax] = c;
+            w1[ax] = pos[ax] - (T)c;
+        }
         long long q = i0[0];
 #pragma unroll
-        for (int a = 1; a < NDIM; ++a) {
-            const int up = (c >> (a - 1)) & 1;
-            w *= up ? w1[a] : ((T)1 - w1[a]);
-            q += (long long)(i0[a] + up) * g.s[a];
+        for (int ax = 1; ax < NDIM; ++ax) q += (long long)i0[ax] * g.s[ax];
+        if (q != q0) {
+            flush(rho, g);
+            q0 = q;
+#pragma unroll
+            for (int c = 0; c < C; ++c) a[c] = b[c] = (T)0;
         }
-        red_pair(rho, q, w * ((T)1 - w1[0]), w * w1[0]);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            T w = m;
+#pragma unroll
+            for (int ax = 1; ax < NDIM; ++ax) {
+                const int up = (c >> (ax - 1)) & 1;
+                w *= up ? w1[ax] : ((T)1 - w1[ax]);
+            }
+            a[c] += w * ((T)1 - w1[0]);
+            b[c] += w * w1[0];
+        }
     }
-}
+};
 
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restrict__ psi,
@@ -239,6 +267,7 @@ __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restri
                 if (ia[a] < g.n[a] - 1) unpack<T>(*reinterpret_cast<const VT*>(psi + base + g.s[a]), hi[a - 1]);
             }
         }
+        StencilAcc<T, NDIM> sa;
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             if (m[k] == (T)0) continue;
@@ -247,8 +276,9 @@ __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restri
 #pragma unroll
             for (int a = 1; a < NDIM; ++a)
                 pos[a] = axis_pos(lo[a - 1][k], c[k + 1], hi[a - 1][k], ia[a], g.n[a], g.power, g.q[a]);
-            deposit_rows<T, NDIM>(rho, g, pos, m[k]);
+            sa.add(rho, g, pos, m[k]);
         }
+        sa.flush(rho, g);
     }
 }
 
