@@ -224,6 +224,8 @@ struct StencilAcc {
     }
 };
 
+constexpr int kPushVecs = 2;                      // 16-byte vectors per thread
+
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restrict__ psi,
                                                                const T* __restrict__ mu,
@@ -233,43 +235,63 @@ __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restri
     if (done && *done) return;
     using VT = typename Vec16<T>::type;
     constexpr int V = Vec16<T>::V;
+    constexpr int NV = kPushVecs, CW = NV * V;        // cells per thread
     const int n0 = g.n[0];
     const long long rows = g.N / n0;
     const long long items = rows * segs;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const long long row = it / segs;
-        const int x0 = ((int)(it - row * segs) * blockDim.x + threadIdx.x) * V;
+        const int x0 = ((int)(it - row * segs) * blockDim.x + threadIdx.x) * CW;
         if (x0 >= n0) continue;
         const long long base = row * n0 + x0;
-        T m[V];
-        unpack<T>(*reinterpret_cast<const VT*>(mu + base), m);
+        T m[CW];
         bool any = false;
 #pragma unroll
-        for (int k = 0; k < V; ++k) any |= (m[k] != (T)0);
+        for (int j = 0; j < NV; ++j) {
+            if (j == 0 || x0 + j * V < n0) unpack<T>(*reinterpret_cast<const VT*>(mu + base + j * V), m + j * V);
+            else
+#pragma unroll
+                for (int k = 0; k < V; ++k) m[j * V + k] = (T)0;
+        }
+#pragma unroll
+        for (int k = 0; k < CW; ++k) any |= (m[k] != (T)0);
         if (!any) continue;
-        T c[V + 2];                                   // psi at x0 - 1 .. x0 + V along the row
-        unpack<T>(*reinterpret_cast<const VT*>(psi + base), c + 1);
-        c[0] = x0 > 0 ? psi[base - 1] : (T)0;
-        c[V + 1] = x0 + V < n0 ? psi[base + V] : (T)0;
+        T c[CW + 2];                                  // psi at x0 - 1 .. x0 + CW along the row
+        T lo[NDIM - 1][CW], hi[NDIM - 1][CW];         // neighbours along axes 1.. (unused at a face)
         int ia[3] = {0, 0, 0};
-        T lo[NDIM - 1][V], hi[NDIM - 1][V];       // neighbours along axes 1.. (unused at a face)
-#pragma unroll
-        for (int a = 0; a < NDIM - 1; ++a)
-#pragma unroll
-            for (int k = 0; k < V; ++k) lo[a][k] = hi[a][k] = c[k + 1];
         {
             long long r = row;
 #pragma unroll
             for (int a = 1; a < NDIM; ++a) {
                 ia[a] = (int)(r % g.n[a]);
                 r /= g.n[a];
-                if (ia[a] > 0) unpack<T>(*reinterpret_cast<const VT*>(psi + base - g.s[a]), lo[a - 1]);
-                if (ia[a] < g.n[a] - 1) unpack<T>(*reinterpret_cast<const VT*>(psi + base + g.s[a]), hi[a - 1]);
             }
         }
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            if (j > 0 && x0 + j * V >= n0) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    c[1 + j * V + k] = (T)0;
+#pragma unroll
+                    for (int a = 0; a < NDIM - 1; ++a) lo[a][j * V + k] = hi[a][j * V + k] = (T)0;
+                }
+                continue;
+            }
+            const long long bj = base + j * V;
+            unpack<T>(*reinterpret_cast<const VT*>(psi + bj), c + 1 + j * V);
+#pragma unroll
+            for (int a = 1; a < NDIM; ++a) {
+                const long long sl = ia[a] > 0 ? g.s[a] : 0, sh = ia[a] < g.n[a] - 1 ? g.s[a] : 0;
+                unpack<T>(*reinterpret_cast<const VT*>(psi + bj - sl), lo[a - 1] + j * V);
+                unpack<T>(*reinterpret_cast<const VT*>(psi + bj + sh), hi[a - 1] + j * V);
+            }
+        }
+        c[0] = x0 > 0 ? psi[base - 1] : (T)0;
+        c[CW + 1] = x0 + CW < n0 ? psi[base + CW] : (T)0;
         StencilAcc<T, NDIM> sa;
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
+        for (int k = 0; k < CW; ++k) {
             if (m[k] == (T)0) continue;
             T pos[3];
             pos[0] = axis_pos(c[k], c[k + 1], c[k + 2], x0 + k, n0, g.power, g.q[0]);
@@ -400,7 +422,8 @@ bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho, 
     const bool rows = g.n[0] % 4 == 0 && aligned16(psi) && aligned16(mu) && aligned16(rho);
     if (rows) {
         constexpr int V = Vec16<T>::V;
-        const int segs = (g.n[0] / V + th - 1) / th;
+        const int per_row = (g.n[0] + V * kPushVecs - 1) / (V * kPushVecs);   // threads per row
+        const int segs = (per_row + th - 1) / th;
         long long items = (g.N / g.n[0]) * segs;
         const long long cap = (long long)num_sms() * 8;
         const int blr = (int)(items < cap ? items : cap);
