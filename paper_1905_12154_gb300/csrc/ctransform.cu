@@ -168,6 +168,92 @@ __device__ __forceinline__ void line_sync(int w, int G)
 
 constexpr int kU = 4;      // column-tile loads each thread keeps in flight
 
+// OR of a predicate over the line group of G threads, which also synchronises
+// it (lines of at most 32 threads: the whole warp, all of whose lines run the
+// same rounds)
+__device__ __forceinline__ bool group_or(bool v, int w, int G)
+{
+    if (G <= 32) return __any_sync(0xffffffffu, v);
+    unsigned r;
+    asm volatile("{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\t"
+                 "bar.red.or.pred po, %2, %3, pi;\n\tselp.u32 %0, 1, 0, po;\n\t}"
+                 : "=r"(r) : "r"(v ? 1u : 0u), "r"(1 + w), "r"(G) : "memory");
+    return r != 0;
+}
+
+constexpr int kFixRounds = 6;          // boundary fix-up rounds before the merges take over
+
+// Parabola indices held in T: differences of indices below 2^24 are exact in
+// FP32, so these give the same values as the integer forms above while
+// avoiding integer-to-float conversions (a fraction of the FP32 rate).
+template <typename T>
+__device__ __forceinline__ bool hidden_t(T a, T fa, T b, T fb, T c, T fc, T hh)
+{
+    const T lhs = (fb - fa) * (c - b) - (fc - fb) * (b - a);
+    const T rhs = hh * (c - a) * (b - a) * (c - b);
+    return lhs >= rhs;
+}
+
+// Phase B as rounds of a parallel fix-up.  A parabola is on the envelope iff
+// its lifted point (j, f_j + hh j^2) is on the lower convex hull of the line's
+// points, and a point that lies on or above a chord between two other points
+// of the line (one on each side) is not.  Each chunk stack is a convex chain,
+// so in their concatenation only the stacks' ends can be reflex: in a round
+// every thread reads the ends of the neighbouring non-empty stacks, then drops
+// its own first entries while they lie above the chord from the left
+// neighbour's last entry, and its last entries while they lie above the chord
+// to the right neighbour's first.  Returns whether any thread of the line
+// group dropped anything (the rounds end when none did: the stacks then form
+// the hull).
+template <int K, typename T>
+__device__ __forceinline__ bool fix_round(const T* f, const short* stk, short* beg, short* end,
+                                          int t, int G, int w, T hh, bool active)
+{
+    using SK = Skew<K>;
+    int b0 = 0, e1 = 0, pa = -1, pc = -1;          // own range, neighbours' end entries
+    if (active) {
+        b0 = beg[t];
+        e1 = end[t];
+        if (e1 > b0) {
+            int pv = t - 1;
+            while (pv >= 0 && beg[pv] == end[pv]) --pv;
+            int nx = t + 1;
+            while (nx < G && beg[nx] == end[nx]) ++nx;
+            if (pv >= 0) pa = end[pv] - 1;
+            if (nx < G) pc = beg[nx];
+        }
+    }
+    if (G <= 32) __syncwarp();                     // every read before any update
+    else asm volatile("bar.sync %0, %1;" :: "r"(1 + w), "r"(G) : "memory");
+    bool dropped = false;
+    if (e1 > b0) {
+        T ja = (T)0, fa = (T)0, jc = (T)0, fc = (T)0;
+        if (pa >= 0) { ja = (T)stk[SK::s(pa)]; fa = f[SK::f(pa)]; }
+        if (pc >= 0) { jc = (T)stk[SK::s(pc)]; fc = f[SK::f(pc)]; }
+        if (pa >= 0) {
+            while (b0 < e1) {
+                T jr, fr;
+                if (b0 + 1 < e1) { jr = (T)stk[SK::s(b0 + 1)]; fr = f[SK::f(b0 + 1)]; }
+                else if (pc >= 0) { jr = jc; fr = fc; }
+                else break;
+                if (!hidden_t(ja, fa, (T)stk[SK::s(b0)], f[SK::f(b0)], jr, fr, hh)) break;
+                ++b0;
+                dropped = true;
+            }
+        }
+        if (pc >= 0) {
+            while (e1 - 1 > b0 &&
+                   hidden_t((T)stk[SK::s(e1 - 2)], f[SK::f(e1 - 2)], (T)stk[SK::s(e1 - 1)],
+                            f[SK::f(e1 - 1)], jc, fc, hh)) {
+                --e1;
+                dropped = true;
+            }
+        }
+        if (dropped) { beg[t] = (short)b0; end[t] = (short)e1; }
+    }
+    return group_or(dropped, w, G);                // also publishes the updates
+}
+
 // BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
 template <typename T, int K, bool CONTIG, bool BATCHED>
 __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtArgs<T>* batch)
@@ -298,15 +384,22 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
             }
         }
         line_sync(w, G);
-        // ---- B: pairwise merges ------------------------------------------------
-        for (int s = 1; s < G; s <<= 1) {
-            if (active && (t & (2 * s - 1)) == 0 && t + s < G) merge_pair<K>(f, stk, beg, end, t, s, n, hh);
-            // the next level merges groups of 4s threads: inside one warp a warp
-            // barrier publishes this level's segment updates, else the line barrier
-            if (4 * s <= 32) __syncwarp();
-            else line_sync(w, G);
+        // ---- B: envelope of the whole line ------------------------------------
+        // Rounds that drop reflex stack ends (see fix_round), then pairwise
+        // merges for lines still changing after kFixRounds rounds.
+        bool moved = true;
+        for (int round = 0; round < kFixRounds && moved; ++round)
+            moved = fix_round<K>(f, stk, beg, end, t, G, w, hh, active);
+        if (moved) {
+            for (int s = 1; s < G; s <<= 1) {
+                if (active && (t & (2 * s - 1)) == 0 && t + s < G) merge_pair<K>(f, stk, beg, end, t, s, n, hh);
+                // the next level merges groups of 4s threads: inside one warp a warp
+                // barrier publishes this level's segment updates, else the line barrier
+                if (4 * s <= 32) __syncwarp();
+                else line_sync(w, G);
+            }
+            line_sync(w, G);
         }
-        line_sync(w, G);
         // ---- C: compaction of (index, value) pairs ---------------------------------
         const int cnt = active ? (end[t] - beg[t]) : 0;
         int incl = cnt;
@@ -430,17 +523,6 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
     }
 }
 
-// Parabola indices held in T: differences of indices below 2^24 are exact in
-// FP32, so these give the same values as the integer forms above while
-// avoiding integer-to-float conversions (a fraction of the FP32 rate).
-template <typename T>
-__device__ __forceinline__ bool hidden_t(T a, T fa, T b, T fb, T c, T fc, T hh)
-{
-    const T lhs = (fb - fa) * (c - b) - (fc - fb) * (b - a);
-    const T rhs = hh * (c - a) * (b - a) * (c - b);
-    return lhs >= rhs;
-}
-
 template <typename T>
 __device__ __forceinline__ T parab_t(T hh, T x, T j, T fj)
 {
@@ -539,19 +621,6 @@ __device__ __forceinline__ void group_sync(int w, int G)
     if (G == 32) __syncwarp();
     else asm volatile("bar.sync %0, %1;" :: "r"(1 + w), "r"(G) : "memory");
 }
-
-// OR of a predicate over one line group, which also synchronises the group
-__device__ __forceinline__ bool group_or(bool v, int w, int G)
-{
-    if (G == 32) return __any_sync(0xffffffffu, v);
-    unsigned r;
-    asm volatile("{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\t"
-                 "bar.red.or.pred po, %2, %3, pi;\n\tselp.u32 %0, 1, 0, po;\n\t}"
-                 : "=r"(r) : "r"(v ? 1u : 0u), "r"(1 + w), "r"(G) : "memory");
-    return r != 0;
-}
-
-constexpr int kFixRounds = 6;          // boundary fix-up rounds before the merges take over
 
 template <typename T, int K>
 __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
@@ -673,58 +742,11 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
         }
         group_sync(w, G);
         // ---- B: envelope of the whole line ------------------------------------
-        // A parabola is on the envelope iff its lifted point (j, f_j + hh j^2)
-        // is on the lower convex hull of the line's points, and a point that
-        // lies on or above a chord between two other points of the line (one
-        // on each side) is not.  Each chunk stack is a convex chain, so in
-        // their concatenation only the stacks' ends can be reflex: in a round
-        // every thread reads the ends of the neighbouring non-empty stacks,
-        // then drops its own first entries while they lie above the chord from
-        // the left neighbour's last entry, and its last entries while they lie
-        // above the chord to the right neighbour's first.  Rounds repeat until
-        // no thread drops anything; a line still changing after kFixRounds
-        // rounds finishes with pairwise merges, which accept any convex stacks.
+        // Rounds that drop reflex stack ends (see fix_round), then pairwise
+        // merges for lines still changing after kFixRounds rounds.
         bool moved = true;
-        for (int round = 0; round < kFixRounds && moved; ++round) {
-            int b0 = beg[t], e1 = end[t];
-            int pa = -1, pc = -1;                  // neighbours' end entries
-            if (e1 > b0) {
-                int pv = t - 1;
-                while (pv >= 0 && beg[pv] == end[pv]) --pv;
-                int nx = t + 1;
-                while (nx < G && beg[nx] == end[nx]) ++nx;
-                if (pv >= 0) pa = end[pv] - 1;
-                if (nx < G) pc = beg[nx];
-            }
-            group_sync(w, G);                      // every read before any update
-            bool dropped = false;
-            if (e1 > b0) {
-                T ja = (T)0, fa = (T)0, jc = (T)0, fc = (T)0;
-                if (pa >= 0) { ja = (T)stk[SK::s(pa)]; fa = f[SK::f(pa)]; }
-                if (pc >= 0) { jc = (T)stk[SK::s(pc)]; fc = f[SK::f(pc)]; }
-                if (pa >= 0) {
-                    while (b0 < e1) {
-                        T jr, fr;
-                        if (b0 + 1 < e1) { jr = (T)stk[SK::s(b0 + 1)]; fr = f[SK::f(b0 + 1)]; }
-                        else if (pc >= 0) { jr = jc; fr = fc; }
-                        else break;
-                        if (!hidden_t(ja, fa, (T)stk[SK::s(b0)], f[SK::f(b0)], jr, fr, hh)) break;
-                        ++b0;
-                        dropped = true;
-                    }
-                }
-                if (pc >= 0) {
-                    while (e1 - 1 > b0 &&
-                           hidden_t((T)stk[SK::s(e1 - 2)], f[SK::f(e1 - 2)], (T)stk[SK::s(e1 - 1)],
-                                    f[SK::f(e1 - 1)], jc, fc, hh)) {
-                        --e1;
-                        dropped = true;
-                    }
-                }
-                if (dropped) { beg[t] = (short)b0; end[t] = (short)e1; }
-            }
-            moved = group_or(dropped, w, G);       // also publishes the updates
-        }
+        for (int round = 0; round < kFixRounds && moved; ++round)
+            moved = fix_round<K>(f, stk, beg, end, t, G, w, hh, true);
         if (moved) {
             for (int s = 1; s < G; s <<= 1) {
                 if ((t & (2 * s - 1)) == 0 && t + s < G) merge_pair_t<K>(f, stk, beg, end, t, s, n, hh);

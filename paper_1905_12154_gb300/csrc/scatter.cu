@@ -224,26 +224,27 @@ struct StencilAcc {
     }
 };
 
-constexpr int kPushVecs = 2;                      // 16-byte vectors per thread
+// 16-byte vectors per thread: two on 2-D grids, one on 3-D grids (whose six
+// neighbour rows already hold a thread's registers)
+template <int NDIM> __host__ __device__ constexpr int push_vecs() { return NDIM == 2 ? 2 : 1; }
 
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restrict__ psi,
                                                                const T* __restrict__ mu,
                                                                T* __restrict__ rho, GridDev g,
-                                                               int segs, const int* done)
+                                                               int per_row, const int* done)
 {
     if (done && *done) return;
     using VT = typename Vec16<T>::type;
     constexpr int V = Vec16<T>::V;
-    constexpr int NV = kPushVecs, CW = NV * V;        // cells per thread
+    constexpr int NV = push_vecs<NDIM>(), CW = NV * V;   // cells per thread
     const int n0 = g.n[0];
     const long long rows = g.N / n0;
-    const long long items = rows * segs;
-    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const long long row = it / segs;
-        const int x0 = ((int)(it - row * segs) * blockDim.x + threadIdx.x) * CW;
-        if (x0 >= n0) continue;
-        const long long base = row * n0 + x0;
+    const unsigned items = (unsigned)(rows * per_row);     // < 2^31 (checked by the launcher)
+    for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+        const unsigned row = it / (unsigned)per_row;
+        const int x0 = (int)(it - row * (unsigned)per_row) * CW;
+        const long long base = (long long)row * n0 + x0;
         T m[CW];
         bool any = false;
 #pragma unroll
@@ -419,16 +420,17 @@ bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho, 
     BFM_CUDA(cudaMemsetAsync(rho, 0, sizeof(T) * g.N, st));
     const GridDev d = dev_grid(g, p);
     const int th = 256, bl = grid_blocks(g.N, th);
-    const bool rows = g.n[0] % 4 == 0 && aligned16(psi) && aligned16(mu) && aligned16(rho);
+    const int CW = Vec16<T>::V * (g.ndim == 2 ? push_vecs<2>() : push_vecs<3>());
+    const int per_row = (g.n[0] + CW - 1) / CW;                          // threads per row
+    const long long items = (g.N / g.n[0]) * per_row;
+    const bool rows = g.n[0] % 4 == 0 && aligned16(psi) && aligned16(mu) && aligned16(rho) &&
+                      items < (1ll << 31);
     if (rows) {
-        constexpr int V = Vec16<T>::V;
-        const int per_row = (g.n[0] + V * kPushVecs - 1) / (V * kPushVecs);   // threads per row
-        const int segs = (per_row + th - 1) / th;
-        long long items = (g.N / g.n[0]) * segs;
+        long long blr = (items + th - 1) / th;
         const long long cap = (long long)num_sms() * 8;
-        const int blr = (int)(items < cap ? items : cap);
-        if (g.ndim == 2) pushforward_rows_kernel<T, 2><<<blr, th, 0, st>>>(psi, mu, rho, d, segs, done);
-        else             pushforward_rows_kernel<T, 3><<<blr, th, 0, st>>>(psi, mu, rho, d, segs, done);
+        if (blr > cap) blr = cap;
+        if (g.ndim == 2) pushforward_rows_kernel<T, 2><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done);
+        else             pushforward_rows_kernel<T, 3><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done);
         BFM_LAUNCH_CHECK("pushforward_rows_kernel");
         return BFM_OK;
     }
