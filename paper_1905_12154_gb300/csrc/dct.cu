@@ -511,7 +511,7 @@ __device__ __noinline__ void stockham_fft_call(float2* z, int n, int t, int T, b
 }
 
 template <int MODE, bool CONTIG, bool BATCHED>
-__global__ void __launch_bounds__(256, 2) dct_fast_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
+__global__ void __launch_bounds__(256, MODE == DCT_MID ? 2 : 3) dct_fast_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
 {
     using C = float2;
     using T = float;
@@ -1004,7 +1004,12 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
     if (s != BFM_OK) return s;
     void* k = select_dct(mode, (int)sizeof(T), axis == 0, false, p.fast != 0);
     BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
-    const int blocks = dct_blocks(p);
+    int blocks = dct_blocks(p);
+    // one wave of resident CTAs, each looping over tiles: a second wave would
+    // start only when first-wave CTAs finish all their tiles
+    int per_sm = 0;
+    BFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, p.threads, p.smem));
+    if (per_sm > 0 && blocks > num_sms() * per_sm) blocks = num_sms() * per_sm;
     const DctArgs<T>* none = nullptr;
     void* args[] = {&a, &none};
     BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(p.threads), args, p.smem, st));
