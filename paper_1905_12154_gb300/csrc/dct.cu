@@ -19,6 +19,7 @@
 //   MID  on the last axis: DCT-II, divide by lambda (zero mode -> 0),
 //        accumulate G = ||g||^2_{H1-dot} in FP64, inverse DCT;
 //   INV  inverse DCT along the axis (optionally out = upd + sigma * g).
+#include <stdint.h>
 #include <string.h>
 
 #include "common.cuh"
@@ -722,6 +723,232 @@ __global__ void __launch_bounds__(256, MODE == DCT_MID ? 2 : 3) dct_fast_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// Rows of 1024, 2048 or 4096 FP32 cells (the axis-0 passes and the middle
+// pass on a transposed copy of 2-D grids): the same line-pair transform as
+// dct_fast_kernel with the length fixed at compile time, so the pass
+// structure, strides and twiddle offsets are constants, and each row moves as
+// float4 vectors, every load of a pair issued before any is used.  One line
+// pair per CTA of n/16 threads; a resident wave of CTAs loops over the pairs.
+// ---------------------------------------------------------------------------
+template <int SIGN, int LOGN>
+__device__ __forceinline__ void fft_fixed(float2* z, int t, const float2* ptw)
+{
+    constexpr int n = 1 << LOGN, T = n / 16, NP = LOGN / 4;
+    float2 v[16];
+#pragma unroll
+    for (int s = 0; s < NP; ++s) {
+        const int Ns = 1 << (4 * s);
+        pass_read<16, SIGN>(z, n, Ns, t, T, ptw, v);
+        __syncthreads();
+        pass_write<16>(z, Ns, t, T, v);
+        __syncthreads();
+    }
+    if (LOGN % 4) {
+        constexpr int R = 1 << (LOGN % 4), Ns = 1 << (4 * NP);
+        pass_read<R, SIGN>(z, n, Ns, t, T, ptw, v);
+        __syncthreads();
+        pass_write<R>(z, Ns, t, T, v);
+        __syncthreads();
+    }
+}
+
+template <int SIGN, int LOGN>
+__device__ __noinline__ void fft_fixed_call(float2* z, int t, const float2* ptw)
+{
+    fft_fixed<SIGN, LOGN>(z, t, ptw);
+}
+
+// position of element j of a line in the even/odd reordering
+// (x0, x2, x4, ..., x5, x3, x1): m(j) = j/2 for even j, n - 1 - (j-1)/2 for odd j
+template <int N>
+__device__ __forceinline__ int reorder_pos(int j) { return (j & 1) ? (N - 1 - (j >> 1)) : (j >> 1); }
+
+template <int MODE, int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 16, (MODE == DCT_MID ? 2 : 3) * (4096 >> LOGN))
+dct_row_kernel(DctArgs<float> a)
+{
+    using C = float2;
+    constexpr int n = 1 << LOGN, T = n / 16, NQ = n / 4, QPT = NQ / T;   // QPT = 4 float4 per row
+    if (a.done && *a.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* z = reinterpret_cast<C*>(smem_raw);
+    __shared__ double red[32];
+    const int t = threadIdx.x;
+    const long long nrows = a.lt.nlines;
+    const long long npairs = (nrows + 1) >> 1;
+    constexpr float inv_n = 1.0f / (float)n;
+    float sig = 0.f;
+    if (MODE == DCT_INV && a.upd) sig = (float)(*a.sigma);
+    double acc = 0.0;
+    Acc<float> gsum;
+
+    for (long long pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        const long long ra = 2 * pr;
+        const bool hb = ra + 1 < nrows;
+        const long long off = ra * n;
+        // ---- load: both rows (and the base rows of FWD) as float4, all in flight at once
+        {
+            const float4* ina = reinterpret_cast<const float4*>(a.in + off);
+            const float4* inb = ina + NQ;
+            const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 xa[QPT], xb[QPT], ba[QPT], bb[QPT];
+#pragma unroll
+            for (int u = 0; u < QPT; ++u) {
+                const int q = t + u * T;
+                xa[u] = ina[q];
+                xb[u] = hb ? inb[q] : zero4;
+            }
+            if (MODE == DCT_FWD && a.base) {
+                const float4* bsa = reinterpret_cast<const float4*>(a.base + off);
+                const float4* bsb = bsa + NQ;
+#pragma unroll
+                for (int u = 0; u < QPT; ++u) {
+                    const int q = t + u * T;
+                    ba[u] = bsa[q];
+                    bb[u] = hb ? bsb[q] : zero4;
+                }
+#pragma unroll
+                for (int u = 0; u < QPT; ++u) {
+                    xa[u].x = ba[u].x - xa[u].x; xa[u].y = ba[u].y - xa[u].y;
+                    xa[u].z = ba[u].z - xa[u].z; xa[u].w = ba[u].w - xa[u].w;
+                    xb[u].x = bb[u].x - xb[u].x; xb[u].y = bb[u].y - xb[u].y;
+                    xb[u].z = bb[u].z - xb[u].z; xb[u].w = bb[u].w - xb[u].w;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < QPT; ++u) {
+                const int j = 4 * (t + u * T);
+                const C c0 = make_float2(xa[u].x, xb[u].x), c1 = make_float2(xa[u].y, xb[u].y);
+                const C c2 = make_float2(xa[u].z, xb[u].z), c3 = make_float2(xa[u].w, xb[u].w);
+                if (MODE == DCT_INV) {
+                    z[padix(j)] = c0; z[padix(j + 1)] = c1; z[padix(j + 2)] = c2; z[padix(j + 3)] = c3;
+                } else {
+                    z[padix(reorder_pos<n>(j))] = c0;     z[padix(reorder_pos<n>(j + 1))] = c1;
+                    z[padix(reorder_pos<n>(j + 2))] = c2; z[padix(reorder_pos<n>(j + 3))] = c3;
+                }
+            }
+        }
+        __syncthreads();
+        if (MODE != DCT_INV) {
+            if (MODE == DCT_MID) fft_fixed_call<-1, LOGN>(z, t, a.ptw);
+            else fft_fixed<-1, LOGN>(z, t, a.ptw);
+            // DCT-II from the FFT of the pair (Makhoul): split the two real
+            // lines' spectra, then twiddle by e^{-i pi k/(2n)}
+            for (int k = t; k <= n / 2; k += T) {
+                const int km = (n - k) & (n - 1);
+                const C Zk = z[padix(k)], Zm = z[padix(km)];
+                C A, Bq;
+                A.x = 0.5f * (Zk.x + Zm.x); A.y = 0.5f * (Zk.y - Zm.y);
+                Bq.x = 0.5f * (Zk.y + Zm.y); Bq.y = 0.5f * (Zm.x - Zk.x);
+                const C dk = a.dtw[k];
+                C outk; outk.x = dk.x * A.x - dk.y * A.y; outk.y = dk.x * Bq.x - dk.y * Bq.y;
+                if (km != k) {
+                    C Am, Bm;
+                    Am.x = 0.5f * (Zm.x + Zk.x); Am.y = 0.5f * (Zm.y - Zk.y);
+                    Bm.x = 0.5f * (Zm.y + Zk.y); Bm.y = 0.5f * (Zk.x - Zm.x);
+                    const C dm = a.dtw[km];
+                    C outm; outm.x = dm.x * Am.x - dm.y * Am.y; outm.y = dm.x * Bm.x - dm.y * Bm.y;
+                    z[padix(km)] = outm;
+                }
+                z[padix(k)] = outk;
+            }
+            __syncthreads();
+        }
+        if (MODE == DCT_MID) {
+            // divide by the eigenvalue lambda(row) + lambda(k) (zero mode -> 0)
+            // and accumulate G = sum w |f^|^2 / lambda (Parseval weights 1, 2)
+            const long long ia = ra, ib = ra + 1;
+            const float La = a.lam_a0[ia], Lb = hb ? a.lam_a0[ib] : 0.f;
+            const float wa = (ia == 0) ? 1.f : 2.f, wb = 2.f;
+            for (int k = t; k < n; k += T) {
+                const float lk = a.lam_axis[k];
+                const float wk = (k == 0) ? 1.f : 2.f;
+                C v = z[padix(k)];
+                const float la = La + lk, lb = Lb + lk;
+                float ga = 0.f, gb = 0.f;
+                if (la > 0.f) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
+                if (hb && lb > 0.f) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
+                v.x = ga; v.y = gb;
+                z[padix(k)] = v;
+            }
+            acc += gsum.take();
+            __syncthreads();
+        }
+        if (MODE != DCT_FWD) {
+            // undo the DCT-II twiddle and recombine the pair's spectra
+            for (int k = t; k <= n / 2; k += T) {
+                const int km = (n - k) & (n - 1);
+                const C Xk = z[padix(k)], Xm = z[padix(km)];
+                const float xam = (k == 0) ? 0.f : Xm.x, xbm = (k == 0) ? 0.f : Xm.y;
+                const C dk = cconj(a.dtw[k]);
+                C Va, Vb;
+                Va.x = dk.x * Xk.x + dk.y * xam; Va.y = dk.y * Xk.x - dk.x * xam;
+                Vb.x = dk.x * Xk.y + dk.y * xbm; Vb.y = dk.y * Xk.y - dk.x * xbm;
+                C Zk; Zk.x = Va.x - Vb.y; Zk.y = Va.y + Vb.x;
+                if (km != k) {
+                    const C dm = cconj(a.dtw[km]);
+                    C Wa, Wb;
+                    Wa.x = dm.x * Xm.x + dm.y * Xk.x; Wa.y = dm.y * Xm.x - dm.x * Xk.x;
+                    Wb.x = dm.x * Xm.y + dm.y * Xk.y; Wb.y = dm.y * Xm.y - dm.x * Xk.y;
+                    C Zm; Zm.x = Wa.x - Wb.y; Zm.y = Wa.y + Wb.x;
+                    z[padix(km)] = Zm;
+                }
+                z[padix(k)] = Zk;
+            }
+            __syncthreads();
+            fft_fixed_call<+1, LOGN>(z, t, a.ptw);
+        }
+        // ---- store: float4 per row (INV with an update reads its rows first) --------
+        {
+            float4* oa = reinterpret_cast<float4*>(a.out + off);
+            float4* ob = oa + NQ;
+            float4 ua[QPT], ub[QPT];
+            if (MODE == DCT_INV && a.upd) {
+                const float4* pa = reinterpret_cast<const float4*>(a.upd + off);
+                const float4* pb = pa + NQ;
+#pragma unroll
+                for (int u = 0; u < QPT; ++u) {
+                    const int q = t + u * T;
+                    ua[u] = pa[q];
+                    ub[u] = hb ? pb[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < QPT; ++u) {
+                const int q = t + u * T, j = 4 * q;
+                C c[4];
+                if (MODE == DCT_FWD) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) c[e] = z[padix(j + e)];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        c[e] = z[padix(reorder_pos<n>(j + e))];
+                        c[e].x *= inv_n;
+                        c[e].y *= inv_n;
+                    }
+                }
+                float4 va = make_float4(c[0].x, c[1].x, c[2].x, c[3].x);
+                float4 vb = make_float4(c[0].y, c[1].y, c[2].y, c[3].y);
+                if (MODE == DCT_INV && a.upd) {
+                    va.x = ua[u].x + sig * va.x; va.y = ua[u].y + sig * va.y;
+                    va.z = ua[u].z + sig * va.z; va.w = ua[u].w + sig * va.w;
+                    vb.x = ub[u].x + sig * vb.x; vb.y = ub[u].y + sig * vb.y;
+                    vb.z = ub[u].z + sig * vb.z; vb.w = ub[u].w + sig * vb.w;
+                }
+                oa[q] = va;
+                if (hb) ob[q] = vb;
+            }
+        }
+        __syncthreads();
+    }
+    if (MODE == DCT_MID && a.part) {
+        const double sacc = block_sum(acc, red);
+        if (threadIdx.x == 0) a.part[blockIdx.x] = sacc * a.gscale;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // tables: twiddles, digit reversal and eigenvalues (computed on the device in FP64)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -982,6 +1209,28 @@ static void* select_dct(int mode, int elem_bytes, bool contig, bool batched, boo
     return dct_kernel<double, DCT_INV>(contig, batched);
 }
 
+// The compile-time row kernel for FP32 rows of 1024-4096 cells whose fields
+// are 16-byte aligned (float4 rows); the middle pass only on 2-D grids (its
+// eigenvalue of the line comes from the one other axis).  NULL: the general
+// kernel handles the pass.
+static void* select_dct_row(int mode, int n, int ndim, const void* in, const void* base,
+                            const void* out, const void* upd)
+{
+    auto al = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+    if (!al(in) || !al(base) || !al(out) || !al(upd)) return nullptr;
+    if (mode == DCT_MID && ndim != 2) return nullptr;
+    if (n == 4096)
+        return mode == DCT_FWD ? (void*)dct_row_kernel<DCT_FWD, 12>
+             : mode == DCT_MID ? (void*)dct_row_kernel<DCT_MID, 12> : (void*)dct_row_kernel<DCT_INV, 12>;
+    if (n == 2048)
+        return mode == DCT_FWD ? (void*)dct_row_kernel<DCT_FWD, 11>
+             : mode == DCT_MID ? (void*)dct_row_kernel<DCT_MID, 11> : (void*)dct_row_kernel<DCT_INV, 11>;
+    if (n == 1024)
+        return mode == DCT_FWD ? (void*)dct_row_kernel<DCT_FWD, 10>
+             : mode == DCT_MID ? (void*)dct_row_kernel<DCT_MID, 10> : (void*)dct_row_kernel<DCT_INV, 10>;
+    return nullptr;
+}
+
 static int dct_blocks(const DctPlan& p)
 {
     long long blocks = p.tiles.ntiles;
@@ -1002,6 +1251,26 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
     DctArgs<T> a;
     bfm_status s = make_dct_args<T>(g, axis, p, tabs, in, base, out, upd, sigma, part, done, &a);
     if (s != BFM_OK) return s;
+    if (sizeof(T) == 4 && axis == 0 && p.fast) {
+        void* rk = select_dct_row(mode, g.n[0], g.ndim, in, base, out, upd);
+        if (rk) {
+            // one line pair per CTA of n/16 threads, one resident wave
+            const int threads = g.n[0] / 16;
+            const size_t smem = (size_t)p.LDZ * sizeof(float2);
+            BFM_CUDA(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int per_sm = 0;
+            BFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rk, threads, smem));
+            long long blocks = (p.tiles.nlines + 1) / 2;
+            const long long cap = (long long)num_sms() * (per_sm > 0 ? per_sm : 1);
+            if (blocks > cap) blocks = cap;
+            if (blocks > kMaxPartials) blocks = kMaxPartials;
+            if (blocks < 1) blocks = 1;
+            void* args[] = {&a};
+            BFM_CUDA(cudaLaunchKernel(rk, dim3((unsigned)blocks), dim3(threads), args, smem, st));
+            if (blocks_used) *blocks_used = (int)blocks;
+            return BFM_OK;
+        }
+    }
     void* k = select_dct(mode, (int)sizeof(T), axis == 0, false, p.fast != 0);
     BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     int blocks = dct_blocks(p);

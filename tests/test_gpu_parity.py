@@ -113,6 +113,19 @@ def test_poisson_fp32(B, shape):
     assert abs(G_got - G_want) <= 2e-5 * abs(G_want)
 
 
+# Rows of 1024, 2048 and 4096 FP32 cells take the compile-time row kernel
+# (float4 rows, one line pair per CTA); odd row counts leave a last pair with
+# one line.
+@pytest.mark.parametrize("shape", [(3, 4096), (16, 4096), (27, 2048), (48, 1024), (9, 1024)], ids=str)
+def test_poisson_fp32_long_rows(B, shape):
+    f = si.random_field(shape, 7).astype(np.float32)
+    g_want, G_want = oracle.poisson(f.astype(np.float64))
+    g_got, G_got = B.bfm_poisson(dev(f, torch.float32))
+    g_got = host(g_got)
+    assert np.max(np.abs(g_got - g_want)) <= 2e-5 * np.max(np.abs(g_want))
+    assert abs(G_got - G_want) <= 2e-5 * abs(G_want)
+
+
 def test_poisson_unsupported_size(B):
     with pytest.raises(B.BfmError) as e:
         B.bfm_poisson(dev(np.zeros((7, 8))))
@@ -362,7 +375,7 @@ def test_long_columns_take_transposed_sweeps(B, shape, dt):
 # rows of 288 or 324 cells take 16 cells per thread and 16 lines per CTA.
 # psi = phi^c of the returned phi is checked cell by cell.
 
-@pytest.mark.parametrize("shape", [(288, 2048), (324, 2048)], ids=str)
+@pytest.mark.parametrize("shape", [(288, 2048), (324, 2048), (16, 4096), (4096, 12)], ids=str)
 def test_solve_long_rows_and_columns_fp32(B, shape):
     mu, nu = long_column_pair(shape, 44)
     ref = oracle.solve(mu, nu, tol=0.0, max_iter=6)
