@@ -763,8 +763,15 @@ __device__ __noinline__ void fft_fixed_call(float2* z, int t, const float2* ptw)
 template <int N>
 __device__ __forceinline__ int reorder_pos(int j) { return (j & 1) ? (N - 1 - (j >> 1)) : (j >> 1); }
 
+// resident CTAs per SM of 256 threads (rows of 4096; shorter rows scale up):
+// the register budget per thread is 65536 / (256 x this)
+constexpr int dct_row_ctas(int mode, int logn)
+{
+    return mode == DCT_FWD ? 3 : mode == DCT_INV ? 3 : (logn == 12 ? 4 : 2);
+}
+
 template <int MODE, int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) / 16, (MODE == DCT_MID ? 2 : 3) * (4096 >> LOGN))
+__global__ void __launch_bounds__((1 << LOGN) / 16, dct_row_ctas(MODE, LOGN) * (4096 >> LOGN))
 dct_row_kernel(DctArgs<float> a)
 {
     using C = float2;
