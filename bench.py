@@ -49,8 +49,13 @@ BYTES_PER_CELL_2D = {
 # copy.  The row sweep then reads and writes (8 bytes); the dual dot of the
 # c-transform output moves into the transpose back, so of the 12 transposes of
 # an iteration 4 read a weight as well (8 x 8 + 4 x 12 bytes).
-BYTES_PER_CELL_2D_TRANSPOSED = dict(BYTES_PER_CELL_2D, ct_pass_axis1=8,
-                                    transpose=(8 * 8 + 4 * 12) / 12)
+# long columns: the axis-1 sweep runs on a transposed copy; of the transposes
+# per iteration, the 4 that bring a c-transform back also read the dual weight
+BYTES_PER_CELL_2D_TRANSPOSED = dict(BYTES_PER_CELL_2D, ct_pass_axis1=8)
+
+
+def transpose_bytes_per_cell(launches_per_iter: float) -> float:
+    return (4 * 12 + (launches_per_iter - 4) * 8) / launches_per_iter
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # of the launches of that kind in one cold-cache ncu capture, summarised in
 # profiles/ct_row_kernel_annulus5g_4096_fp32.md); reported only while the
@@ -378,7 +383,10 @@ def main():
     pk, src = peaks()
     kinds = {k: v for k, v in prof.items() if not k.startswith("_")}
     launches = round(sum(c for _, c in kinds.values()) / prof_steps * args.steps)
-    table = BYTES_PER_CELL_2D_TRANSPOSED if kinds.get("transpose", (0, 0))[1] else BYTES_PER_CELL_2D
+    table = BYTES_PER_CELL_2D
+    if kinds.get("transpose", (0, 0))[1]:
+        table = dict(BYTES_PER_CELL_2D_TRANSPOSED,
+                     transpose=transpose_bytes_per_cell(kinds["transpose"][1] / prof_steps))
     dom = max((k for k in kinds if k in table and kinds[k][1]), key=lambda k: kinds[k][0])
     ms, cnt = kinds[dom]
     bytes_per_launch = table[dom] * N

@@ -94,6 +94,51 @@ __device__ __forceinline__ void dft_small(int r, C* u)
     }
 }
 
+// One radix-R stage of the forward decimation-in-time network: butterfly b
+// (sub-transform B = b / L, offset k1 = b mod L) combines z[B Lp + k1 + q L],
+// q < R, twiddled by e^{-2 pi i q k1 tstep / n}.  R is a compile-time
+// constant so the butterfly's values stay in registers.
+template <int R, typename C>
+__device__ __forceinline__ void dit_stage(C* z, const C* tw, int t, int G, int nb, int L, int Lp,
+                                          int tstep, unsigned mg)
+{
+    for (int b = t; b < nb; b += G) {
+        const int B = div_by(b, L, mg), k1 = b - B * L;
+        const int base = B * Lp + k1;
+        C u[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            C v = z[base + q * L];
+            if (q) v = cmul(v, tw[q * k1 * tstep]);
+            u[q] = v;
+        }
+        dft_small<-1>(R, u);
+#pragma unroll
+        for (int q = 0; q < R; ++q) z[base + q * L] = u[q];
+    }
+}
+
+// The matching stage of the inverse decimation-in-frequency network.
+template <int R, typename C>
+__device__ __forceinline__ void dif_stage(C* z, const C* tw, int t, int G, int nb, int L, int Lp,
+                                          int tstep, unsigned mg)
+{
+    for (int b = t; b < nb; b += G) {
+        const int B = div_by(b, L, mg), k1 = b - B * L;
+        const int base = B * Lp + k1;
+        C u[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) u[q] = z[base + q * L];
+        dft_small<+1>(R, u);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            C v = u[q];
+            if (q) v = cmul(v, cconj(tw[q * k1 * tstep]));
+            z[base + q * L] = v;
+        }
+    }
+}
+
 // BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
 template <typename T, int MODE, bool CONTIG, bool BATCHED>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024, 1)
@@ -124,31 +169,51 @@ dct_pass_kernel(DctArgs<T> a0, const DctArgs<T>* batch)
         const int np = (tl.wact + 1) / 2;
         // ---- load ------------------------------------------------------------
         {
-            // CONTIG: one row pair after another; interleaved: pairs fastest
+            // CONTIG: one row pair after another; interleaved: pairs fastest.
+            // Each thread issues U loads (and their base loads) before storing
+            // any, so a tile's loads overlap instead of forming a chain.
+            constexpr int U = 4;
             const int np_pow = CONTIG ? 1 : (1 << a.lnp);
             const int per = CONTIG ? n : np_pow * n;
             const int reps = CONTIG ? np : 1;
+            const int bd = blockDim.x;
             for (int q0 = 0; q0 < reps; ++q0)
-            for (int e = tid; e < per; e += blockDim.x) {
-                int q, j;
-                if (CONTIG) { q = q0; j = e; }
-                else        { q = e & (np_pow - 1); j = e >> a.lnp; }
-                if (q >= np) continue;
-                const int lb = 2 * q + 1;
-                const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
-                T xa = a.in[ada];
-                T xb = (T)0;
-                if (lb < tl.wact) xb = a.in[ada + tl.lstride];
-                if (MODE == DCT_FWD && a.base) {
-                    xa = a.base[ada] - xa;
-                    if (lb < tl.wact) xb = a.base[ada + tl.lstride] - xb;
+            for (int e0 = tid; e0 < per; e0 += U * bd) {
+                T xa[U], xb[U], ba[U], bb[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * bd;
+                    int q, j;
+                    if (CONTIG) { q = q0; j = e; }
+                    else        { q = e & (np_pow - 1); j = e >> a.lnp; }
+                    xa[u] = xb[u] = ba[u] = bb[u] = (T)0;
+                    if (e < per && q < np) {
+                        const bool hb = 2 * q + 1 < tl.wact;
+                        const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                        xa[u] = a.in[ada];
+                        if (hb) xb[u] = a.in[ada + tl.lstride];
+                        if (MODE == DCT_FWD && a.base) {
+                            ba[u] = a.base[ada];
+                            if (hb) bb[u] = a.base[ada + tl.lstride];
+                        }
+                    }
                 }
-                C v; v.x = xa; v.y = xb;
-                if (MODE == DCT_INV) {
-                    zs[(size_t)q * a.LDZ + j] = v;                       // natural order
-                } else {
-                    const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
-                    zs[(size_t)q * a.LDZ + a.drev[m]] = v;               // DIT input order
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * bd;
+                    int q, j;
+                    if (CONTIG) { q = q0; j = e; }
+                    else        { q = e & (np_pow - 1); j = e >> a.lnp; }
+                    if (e >= per || q >= np) continue;
+                    C v;
+                    if (MODE == DCT_FWD && a.base) { v.x = ba[u] - xa[u]; v.y = bb[u] - xb[u]; }
+                    else { v.x = xa[u]; v.y = xb[u]; }
+                    if (MODE == DCT_INV) {
+                        zs[(size_t)q * a.LDZ + j] = v;                       // natural order
+                    } else {
+                        const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
+                        zs[(size_t)q * a.LDZ + a.drev[m]] = v;               // DIT input order
+                    }
                 }
             }
         }
@@ -164,18 +229,9 @@ dct_pass_kernel(DctArgs<T> a0, const DctArgs<T>* batch)
                 const unsigned mg = a.mag[s];
                 const int nb = (r == 4) ? (n >> 2) : (r == 2 ? (n >> 1) : n / 3);
                 if (active) {
-                    for (int b = t; b < nb; b += G) {
-                        const int B = div_by(b, L, mg), k1 = b - B * L;
-                        const int base = B * Lp + k1;
-                        C u[4];
-                        for (int q = 0; q < r; ++q) {
-                            C v = z[base + q * L];
-                            if (q) v = cmul(v, a.tw[q * k1 * tstep]);
-                            u[q] = v;
-                        }
-                        dft_small<-1>(r, u);
-                        for (int q = 0; q < r; ++q) z[base + q * L] = u[q];
-                    }
+                    if (r == 4) dit_stage<4>(z, a.tw, t, G, nb, L, Lp, tstep, mg);
+                    else if (r == 2) dit_stage<2>(z, a.tw, t, G, nb, L, Lp, tstep, mg);
+                    else dit_stage<3>(z, a.tw, t, G, nb, L, Lp, tstep, mg);
                 }
                 __syncthreads();
             }
@@ -267,50 +323,64 @@ dct_pass_kernel(DctArgs<T> a0, const DctArgs<T>* batch)
                 const unsigned mg = a.mag[s];
                 const int nb = (r == 4) ? (n >> 2) : (r == 2 ? (n >> 1) : n / 3);
                 if (active) {
-                    for (int b = t; b < nb; b += G) {
-                        const int B = div_by(b, L, mg), k1 = b - B * L;
-                        const int base = B * Lp + k1;
-                        C u[4];
-                        for (int q = 0; q < r; ++q) u[q] = z[base + q * L];
-                        dft_small<+1>(r, u);
-                        for (int q = 0; q < r; ++q) {
-                            C v = u[q];
-                            if (q) v = cmul(v, cconj(a.tw[q * k1 * tstep]));
-                            z[base + q * L] = v;
-                        }
-                    }
+                    if (r == 4) dif_stage<4>(z, a.tw, t, G, nb, L, Lp, tstep, mg);
+                    else if (r == 2) dif_stage<2>(z, a.tw, t, G, nb, L, Lp, tstep, mg);
+                    else dif_stage<3>(z, a.tw, t, G, nb, L, Lp, tstep, mg);
                 }
                 __syncthreads();
             }
         }
         // ---- store ------------------------------------------------------------------
         {
+            // the potential update reads its U values before any store
+            constexpr int U = 4;
             const int np_pow = CONTIG ? 1 : (1 << a.lnp);
             const int per = CONTIG ? n : np_pow * n;
             const int reps = CONTIG ? np : 1;
+            const int bd = blockDim.x;
             for (int q0 = 0; q0 < reps; ++q0)
-            for (int e = tid; e < per; e += blockDim.x) {
-                int q, j;
-                if (CONTIG) { q = q0; j = e; }
-                else        { q = e & (np_pow - 1); j = e >> a.lnp; }
-                if (q >= np) continue;
-                const int lb = 2 * q + 1;
-                const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
-                C v;
-                if (MODE == DCT_FWD) {
-                    v = zs[(size_t)q * a.LDZ + j];
-                } else {
-                    const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
-                    v = zs[(size_t)q * a.LDZ + a.drev[m]];
-                    v.x *= inv_n;
-                    v.y *= inv_n;
-                }
+            for (int e0 = tid; e0 < per; e0 += U * bd) {
+                T ua[U], ub[U];
                 if (MODE == DCT_INV && a.upd) {
-                    a.out[ada] = a.upd[ada] + sig * v.x;
-                    if (lb < tl.wact) a.out[ada + tl.lstride] = a.upd[ada + tl.lstride] + sig * v.y;
-                } else {
-                    a.out[ada] = v.x;
-                    if (lb < tl.wact) a.out[ada + tl.lstride] = v.y;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int e = e0 + u * bd;
+                        int q, j;
+                        if (CONTIG) { q = q0; j = e; }
+                        else        { q = e & (np_pow - 1); j = e >> a.lnp; }
+                        ua[u] = ub[u] = (T)0;
+                        if (e < per && q < np) {
+                            const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                            ua[u] = a.upd[ada];
+                            if (2 * q + 1 < tl.wact) ub[u] = a.upd[ada + tl.lstride];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * bd;
+                    int q, j;
+                    if (CONTIG) { q = q0; j = e; }
+                    else        { q = e & (np_pow - 1); j = e >> a.lnp; }
+                    if (e >= per || q >= np) continue;
+                    const int lb = 2 * q + 1;
+                    const long long ada = tl.base0 + (long long)(2 * q) * tl.lstride + (long long)j * lt.es;
+                    C v;
+                    if (MODE == DCT_FWD) {
+                        v = zs[(size_t)q * a.LDZ + j];
+                    } else {
+                        const int m = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);
+                        v = zs[(size_t)q * a.LDZ + a.drev[m]];
+                        v.x *= inv_n;
+                        v.y *= inv_n;
+                    }
+                    if (MODE == DCT_INV && a.upd) {
+                        a.out[ada] = ua[u] + sig * v.x;
+                        if (lb < tl.wact) a.out[ada + tl.lstride] = ub[u] + sig * v.y;
+                    } else {
+                        a.out[ada] = v.x;
+                        if (lb < tl.wact) a.out[ada + tl.lstride] = v.y;
+                    }
                 }
             }
         }
