@@ -1026,6 +1026,267 @@ dct_row_kernel(DctArgs<float> a)
 }
 
 // ---------------------------------------------------------------------------
+// Lines of 384 FP32 cells (the 3-D workload's axes): one warp per line pair,
+// 12 complex values per lane, a register Stockham FFT with radices
+// 4 x 4 x 4 x 6 whose passes synchronise only the warp.  A CTA holds 32 lines
+// (16 pairs): 32 neighbouring rows, or 32 neighbouring lines of an axis > 0
+// whose element j is a run of 32 consecutive floats; both move as float4.
+// ---------------------------------------------------------------------------
+template <int SIGN>
+__device__ __forceinline__ void dft6(float2* u)
+{
+    // m = 2 m1 + m2: three-point transforms over m1, twiddle w6^(m2 k1), two-point over m2
+    const float s3 = (float)SIGN * 0.86602540378443864676f;   // sin(2 pi/3) with sign
+    float2 y[2][3];
+#pragma unroll
+    for (int m2 = 0; m2 < 2; ++m2) {
+        const float2 u0 = u[m2], u1 = u[2 + m2], u2 = u[4 + m2];
+        const float2 t1 = cadd(u1, u2), t2 = csub(u1, u2);
+        const float2 m = make_float2(u0.x - 0.5f * t1.x, u0.y - 0.5f * t1.y);
+        const float2 it2 = make_float2(-s3 * t2.y, s3 * t2.x);
+        y[m2][0] = cadd(u0, t1);
+        y[m2][1] = cadd(m, it2);
+        y[m2][2] = csub(m, it2);
+    }
+    // w6 = e^{SIGN i pi/3} = (1/2, SIGN sqrt3/2), w6^2 = (-1/2, SIGN sqrt3/2)
+    const float2 a1 = y[1][1], a2 = y[1][2];
+    y[1][1] = make_float2(0.5f * a1.x - s3 * a1.y, 0.5f * a1.y + s3 * a1.x);
+    y[1][2] = make_float2(-0.5f * a2.x - s3 * a2.y, -0.5f * a2.y + s3 * a2.x);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        u[k1] = cadd(y[0][k1], y[1][k1]);
+        u[k1 + 3] = csub(y[0][k1], y[1][k1]);
+    }
+}
+
+// One Stockham pass of radix R and stride Ns over a line of N held by the
+// T = N / V lanes of a warp, V values per lane (V / R butterflies each).
+template <int N, int V, int R, int Ns, int SIGN>
+__device__ __forceinline__ void passv(float2* z, int t, const float2* ptw)
+{
+    constexpr int T = N / V, B = V / R;
+    float2 v[V];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = t + b * T;
+        const int k = j % Ns;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b * R + r] = z[padix(j + r * (N / R))];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r)
+                v[b * R + r] = cmul_sgn<SIGN>(v[b * R + r], ptw[(Ns - 1) + (r - 1) * Ns + k]);
+        }
+        if (R == 4) r4<SIGN>(v, b * R, 1);
+        else dft6<SIGN>(v + b * R);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = t + b * T;
+        const int k = j % Ns;
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) z[padix(base + r * Ns)] = v[b * R + r];
+    }
+    __syncwarp();
+}
+
+template <int SIGN>
+__device__ __forceinline__ void fft384(float2* z, int t, const float2* ptw)
+{
+    passv<384, 12, 4, 1, SIGN>(z, t, ptw);
+    passv<384, 12, 4, 4, SIGN>(z, t, ptw);
+    passv<384, 12, 4, 16, SIGN>(z, t, ptw);
+    passv<384, 12, 6, 64, SIGN>(z, t, ptw);
+}
+
+template <int MODE, bool CONTIG>
+__global__ void __launch_bounds__(512, 2) dct384_kernel(DctArgs<float> a)
+{
+    using C = float2;
+    constexpr int N = 384, LDZ = N + N / 16 + 1;
+    if (a.done && *a.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* zs = reinterpret_cast<C*>(smem_raw);
+    __shared__ double red[32];
+    const LineTiles& lt = a.lt;
+    const int tid = threadIdx.x, lane = tid & 31, pw = tid >> 5;     // warp = line pair
+    C* z = zs + pw * LDZ;
+    constexpr float inv_n = 1.0f / (float)N;
+    float sig = 0.f;
+    if (MODE == DCT_INV && a.upd) sig = (float)(*a.sigma);
+    double acc = 0.0;
+    Acc<float> gsum;
+
+    for (long long tile = blockIdx.x; tile < lt.ntiles; tile += gridDim.x) {
+        const Tile tl = tile_at(lt, tile);               // every tile holds W lines
+        // ---- load: 32 lines x 384 = 3072 float4, six per thread ----------------------
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float4 x[3], b[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int e = tid + 512 * (3 * h + u);
+                long long ad;
+                if (CONTIG) ad = tl.base0 + (long long)(tid >> 4) * N + 4 * ((tid & 15) + 16 * (3 * h + u));
+                else ad = tl.base0 + 4 * (e & 7) + (long long)(e >> 3) * lt.es;
+                x[u] = *reinterpret_cast<const float4*>(a.in + ad);
+                if (MODE == DCT_FWD && a.base) b[u] = *reinterpret_cast<const float4*>(a.base + ad);
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int e = tid + 512 * (3 * h + u);
+                float4 v = x[u];
+                if (MODE == DCT_FWD && a.base) {
+                    v.x = b[u].x - v.x; v.y = b[u].y - v.y; v.z = b[u].z - v.z; v.w = b[u].w - v.w;
+                }
+                if (CONTIG) {
+                    // row r = tid / 16 (16 threads per row), elements j .. j+3:
+                    // component r & 1 of pair r / 2
+                    const int r = tid >> 4, j = 4 * ((tid & 15) + 16 * (3 * h + u));
+                    float* zr = reinterpret_cast<float*>(zs + (r >> 1) * LDZ) + (r & 1);
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int m = (MODE == DCT_INV) ? j + c : reorder_pos<N>(j + c);
+                        zr[2 * padix(m)] = vv[c];
+                    }
+                } else {
+                    // element j of lines 4q .. 4q+3: pairs 2q and 2q + 1
+                    const int q = e & 7, j = e >> 3;
+                    const int m = (MODE == DCT_INV) ? j : reorder_pos<N>(j);
+                    zs[(2 * q) * LDZ + padix(m)] = make_float2(v.x, v.y);
+                    zs[(2 * q + 1) * LDZ + padix(m)] = make_float2(v.z, v.w);
+                }
+            }
+        }
+        __syncthreads();
+        if (MODE != DCT_INV) {
+            fft384<-1>(z, lane, a.ptw);
+            for (int k = lane; k <= N / 2; k += 32) {
+                const int km = (k == 0) ? 0 : N - k;
+                const C Zk = z[padix(k)], Zm = z[padix(km)];
+                C A, Bq;
+                A.x = 0.5f * (Zk.x + Zm.x); A.y = 0.5f * (Zk.y - Zm.y);
+                Bq.x = 0.5f * (Zk.y + Zm.y); Bq.y = 0.5f * (Zm.x - Zk.x);
+                const C dk = a.dtw[k];
+                C outk; outk.x = dk.x * A.x - dk.y * A.y; outk.y = dk.x * Bq.x - dk.y * Bq.y;
+                if (km != k) {
+                    C Am, Bm;
+                    Am.x = 0.5f * (Zm.x + Zk.x); Am.y = 0.5f * (Zm.y - Zk.y);
+                    Bm.x = 0.5f * (Zm.y + Zk.y); Bm.y = 0.5f * (Zk.x - Zm.x);
+                    const C dm = a.dtw[km];
+                    C outm; outm.x = dm.x * Am.x - dm.y * Am.y; outm.y = dm.x * Bm.x - dm.y * Bm.y;
+                    z[padix(km)] = outm;
+                }
+                z[padix(k)] = outk;
+            }
+            __syncwarp();
+        }
+        if (MODE == DCT_MID) {
+            // eigenvalue of the pair's lines along the other axes (Parseval weights 1 or 2)
+            const int ia = (CONTIG ? (int)tl.outer : tl.i0) + 2 * pw, ib = ia + 1;
+            float La = a.lam_a0[ia], Lb = a.lam_a0[ib];
+            float wa = (ia == 0) ? 1.f : 2.f, wb = 2.f;
+            if (a.lam_a1) {
+                const int jo = (int)tl.outer;
+                La += a.lam_a1[jo]; Lb += a.lam_a1[jo];
+                const float wo = (jo == 0) ? 1.f : 2.f;
+                wa *= wo; wb *= wo;
+            }
+            for (int k = lane; k < N; k += 32) {
+                const float lk = a.lam_axis[k];
+                const float wk = (k == 0) ? 1.f : 2.f;
+                C v = z[padix(k)];
+                const float la = La + lk, lb = Lb + lk;
+                float ga = 0.f, gb = 0.f;
+                if (la > 0.f) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
+                if (lb > 0.f) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
+                v.x = ga; v.y = gb;
+                z[padix(k)] = v;
+            }
+            acc += gsum.take();
+            __syncwarp();
+        }
+        if (MODE != DCT_FWD) {
+            for (int k = lane; k <= N / 2; k += 32) {
+                const int km = (k == 0) ? 0 : N - k;
+                const C Xk = z[padix(k)], Xm = z[padix(km)];
+                const float xam = (k == 0) ? 0.f : Xm.x, xbm = (k == 0) ? 0.f : Xm.y;
+                const C dk = cconj(a.dtw[k]);
+                C Va, Vb;
+                Va.x = dk.x * Xk.x + dk.y * xam; Va.y = dk.y * Xk.x - dk.x * xam;
+                Vb.x = dk.x * Xk.y + dk.y * xbm; Vb.y = dk.y * Xk.y - dk.x * xbm;
+                C Zk; Zk.x = Va.x - Vb.y; Zk.y = Va.y + Vb.x;
+                if (km != k) {
+                    const C dm = cconj(a.dtw[km]);
+                    C Wa, Wb;
+                    Wa.x = dm.x * Xm.x + dm.y * Xk.x; Wa.y = dm.y * Xm.x - dm.x * Xk.x;
+                    Wb.x = dm.x * Xm.y + dm.y * Xk.y; Wb.y = dm.y * Xm.y - dm.x * Xk.y;
+                    C Zm; Zm.x = Wa.x - Wb.y; Zm.y = Wa.y + Wb.x;
+                    z[padix(km)] = Zm;
+                }
+                z[padix(k)] = Zk;
+            }
+            __syncwarp();
+            fft384<+1>(z, lane, a.ptw);
+        }
+        __syncthreads();
+        // ---- store (the potential update reads its values first) ---------------------
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float4 up[3];
+            if (MODE == DCT_INV && a.upd) {
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    const int e = tid + 512 * (3 * h + u);
+                    long long ad;
+                    if (CONTIG) ad = tl.base0 + (long long)(tid >> 4) * N + 4 * ((tid & 15) + 16 * (3 * h + u));
+                    else ad = tl.base0 + 4 * (e & 7) + (long long)(e >> 3) * lt.es;
+                    up[u] = *reinterpret_cast<const float4*>(a.upd + ad);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int e = tid + 512 * (3 * h + u);
+                long long ad;
+                float4 v;
+                if (CONTIG) {
+                    const int r = tid >> 4, j = 4 * ((tid & 15) + 16 * (3 * h + u));
+                    ad = tl.base0 + (long long)r * N + j;
+                    const float* zr = reinterpret_cast<const float*>(zs + (r >> 1) * LDZ) + (r & 1);
+                    float vv[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int m = (MODE == DCT_FWD) ? j + c : reorder_pos<N>(j + c);
+                        vv[c] = zr[2 * padix(m)];
+                    }
+                    v = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                } else {
+                    const int q = e & 7, j = e >> 3;
+                    ad = tl.base0 + 4 * q + (long long)j * lt.es;
+                    const int m = (MODE == DCT_FWD) ? j : reorder_pos<N>(j);
+                    const C p0 = zs[(2 * q) * LDZ + padix(m)], p1 = zs[(2 * q + 1) * LDZ + padix(m)];
+                    v = make_float4(p0.x, p0.y, p1.x, p1.y);
+                }
+                if (MODE != DCT_FWD) { v.x *= inv_n; v.y *= inv_n; v.z *= inv_n; v.w *= inv_n; }
+                if (MODE == DCT_INV && a.upd) {
+                    v.x = up[u].x + sig * v.x; v.y = up[u].y + sig * v.y;
+                    v.z = up[u].z + sig * v.z; v.w = up[u].w + sig * v.w;
+                }
+                *reinterpret_cast<float4*>(a.out + ad) = v;
+            }
+        }
+        __syncthreads();
+    }
+    if (MODE == DCT_MID && a.part) {
+        const double sacc = block_sum(acc, red);
+        if (threadIdx.x == 0) a.part[blockIdx.x] = sacc * a.gscale;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // tables: twiddles, digit reversal and eigenvalues (computed on the device in FP64)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -1071,12 +1332,22 @@ bool fft_radices(int n, FftRadices* rs)
 
 static bool fast_radices(int n, int* nst, int* rad);
 
-// FP32 power-of-two lines from 32 cells run the register FFT and carry its
-// pass twiddle table
+// Radices of the 384-point register FFT (dct384_kernel): 4 x 4 x 4 x 6
+static bool radices_384(int n, int* nst, int* rad)
+{
+    if (n != 384) return false;
+    rad[0] = rad[1] = rad[2] = 4;
+    rad[3] = 6;
+    *nst = 4;
+    return true;
+}
+
+// FP32 power-of-two lines from 32 cells and FP32 lines of 384 run a register
+// FFT and carry its pass twiddle table
 static bool has_pass_table(int n, int elem_bytes)
 {
     int nst, rad[8];
-    return elem_bytes == 4 && fast_radices(n, &nst, rad);
+    return elem_bytes == 4 && (fast_radices(n, &nst, rad) || radices_384(n, &nst, rad));
 }
 
 size_t axis_table_bytes(int n, int elem_bytes)
@@ -1137,7 +1408,7 @@ bfm_status fill_axis_tables(int n, AxisTables* t, unsigned char* ws, cudaStream_
     BFM_LAUNCH_CHECK("fill_tables_kernel");
     if (t->ptw) {
         PassRadices pr;
-        fast_radices(n, &pr.nst, pr.rad);
+        if (!fast_radices(n, &pr.nst, pr.rad)) radices_384(n, &pr.nst, pr.rad);
         fill_pass_table_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, reinterpret_cast<float2*>(t->ptw), pr);
         BFM_LAUNCH_CHECK("fill_pass_table_kernel");
     }
@@ -1328,6 +1599,32 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
     DctArgs<T> a;
     bfm_status s = make_dct_args<T>(g, axis, p, tabs, in, base, out, upd, sigma, part, done, &a);
     if (s != BFM_OK) return s;
+    if (sizeof(T) == 4 && g.n[axis] == 384 && tabs[axis].ptw) {
+        // tiles of 32 whole lines, float4 on both sides
+        auto al = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+        const bool full = axis == 0 ? (g.N / 384) % 32 == 0 : g.n[0] % 32 == 0;
+        if (full && al(in) && al(base) && al(out) && al(upd)) {
+            a.lt = make_tiles(g, axis, 32);
+            void* k384 = axis == 0
+                ? (mode == DCT_FWD ? (void*)dct384_kernel<DCT_FWD, true>
+                   : mode == DCT_MID ? (void*)dct384_kernel<DCT_MID, true> : (void*)dct384_kernel<DCT_INV, true>)
+                : (mode == DCT_FWD ? (void*)dct384_kernel<DCT_FWD, false>
+                   : mode == DCT_MID ? (void*)dct384_kernel<DCT_MID, false> : (void*)dct384_kernel<DCT_INV, false>);
+            const size_t smem = (size_t)16 * (384 + 384 / 16 + 1) * sizeof(float2);
+            BFM_CUDA(cudaFuncSetAttribute(k384, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int per_sm = 0;
+            BFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k384, 512, smem));
+            long long blocks = a.lt.ntiles;
+            const long long cap = (long long)num_sms() * (per_sm > 0 ? per_sm : 1);
+            if (blocks > cap) blocks = cap;
+            if (blocks > kMaxPartials) blocks = kMaxPartials;
+            if (blocks < 1) blocks = 1;
+            void* args[] = {&a};
+            BFM_CUDA(cudaLaunchKernel(k384, dim3((unsigned)blocks), dim3(512), args, smem, st));
+            if (blocks_used) *blocks_used = (int)blocks;
+            return BFM_OK;
+        }
+    }
     if (sizeof(T) == 4 && axis == 0 && p.fast) {
         void* rk = select_dct_row(mode, g.n[0], g.ndim, in, base, out, upd);
         if (rk) {

@@ -126,6 +126,21 @@ def test_poisson_fp32_long_rows(B, shape):
     assert abs(G_got - G_want) <= 2e-5 * abs(G_want)
 
 
+# Lines of 384 FP32 cells take the register FFT of radices 4 x 4 x 4 x 6 with
+# tiles of 32 whole lines: rows (axis 0), interleaved lines of axis 1 and the
+# middle pass along the last axis (2-D and 3-D, with the eigenvalues of both
+# other axes).
+@pytest.mark.parametrize("shape", [(64, 384), (384, 32), (384, 8, 32), (32, 384, 64), (24, 32, 384)],
+                         ids=str)
+def test_poisson_fp32_384(B, shape):
+    f = si.random_field(shape, 8).astype(np.float32)
+    g_want, G_want = oracle.poisson(f.astype(np.float64))
+    g_got, G_got = B.bfm_poisson(dev(f, torch.float32))
+    g_got = host(g_got)
+    assert np.max(np.abs(g_got - g_want)) <= 2e-5 * np.max(np.abs(g_want))
+    assert abs(G_got - G_want) <= 2e-5 * abs(G_want)
+
+
 def test_poisson_unsupported_size(B):
     with pytest.raises(B.BfmError) as e:
         B.bfm_poisson(dev(np.zeros((7, 8))))
@@ -215,6 +230,20 @@ def test_solve_3d_fp64(B):
     r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=6)
     assert np.max(np.abs(r["dual"] - ref["dual"])) < 1e-11
     assert abs(r["w2sq"] - ref["w2sq"]) < 1e-11
+
+
+def test_solve_3d_fp32_384_lines(B):
+    """FP32 3-D solve whose axis-0 and axis-2 lines have 384 cells (the
+    384-point register FFT on rows and on the middle pass)."""
+    shape = (384, 4, 384)
+    rng = np.random.default_rng(46)
+    mu = si.normalise(si.gaussian_mixture(shape, rng.uniform(0.3, 0.7, (2, 3)), [0.12, 0.08]))
+    nu = si.normalise(si.gaussian_mixture(shape, rng.uniform(0.3, 0.7, (3, 3)), [0.1, 0.1, 0.07]))
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=3)
+    r = B.bfm_solve(dev(mu, torch.float32), dev(nu, torch.float32), tol=0.0, max_iter=3)
+    assert r["iters"] == 3
+    assert abs(r["w2sq"] - ref["w2sq"]) / ref["w2sq"] < 1e-5
+    assert np.max(np.abs(r["resid"] - ref["resid"])) < 1e-3
 
 
 def test_solve_fp32_matches_fp64_oracle(B):
