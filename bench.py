@@ -49,13 +49,22 @@ BYTES_PER_CELL_2D = {
 # copy.  The row sweep then reads and writes (8 bytes); the dual dot of the
 # c-transform output moves into the transpose back, so of the 12 transposes of
 # an iteration 4 read a weight as well (8 x 8 + 4 x 12 bytes).
-# long columns: the axis-1 sweep runs on a transposed copy; of the transposes
-# per iteration, the 4 that bring a c-transform back also read the dual weight
+# Long columns: the axis-1 sweep runs on a transposed copy.  Of the L
+# transposes per iteration, 4 belong to the two Poisson solves and one to each
+# c-transform; a c-transform with a second one (back to its input's layout)
+# takes the dot of its output there (L - 8 of them), the others (12 - L) leave
+# their output transposed and take that dot in the second sweep's store.
 BYTES_PER_CELL_2D_TRANSPOSED = dict(BYTES_PER_CELL_2D, ct_pass_axis1=8)
 
 
 def transpose_bytes_per_cell(launches_per_iter: float) -> float:
-    return (4 * 12 + (launches_per_iter - 4) * 8) / launches_per_iter
+    dots = launches_per_iter - 8
+    return (dots * 12 + (launches_per_iter - dots) * 8) / launches_per_iter
+
+
+def second_sweep_bytes_per_cell(transposes_per_iter: float) -> float:
+    flips = 12 - transposes_per_iter
+    return (8 * (4 - flips) + 12 * flips) / 4
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # of the launches of that kind in one cold-cache ncu capture, summarised in
 # profiles/ct_row_kernel_annulus5g_4096_fp32.md); reported only while the
@@ -385,8 +394,9 @@ def main():
     launches = round(sum(c for _, c in kinds.values()) / prof_steps * args.steps)
     table = BYTES_PER_CELL_2D
     if kinds.get("transpose", (0, 0))[1]:
-        table = dict(BYTES_PER_CELL_2D_TRANSPOSED,
-                     transpose=transpose_bytes_per_cell(kinds["transpose"][1] / prof_steps))
+        lt = kinds["transpose"][1] / prof_steps
+        table = dict(BYTES_PER_CELL_2D_TRANSPOSED, transpose=transpose_bytes_per_cell(lt),
+                     ct_pass_axis1=second_sweep_bytes_per_cell(lt))
     dom = max((k for k in kinds if k in table and kinds[k][1]), key=lambda k: kinds[k][0])
     ms, cnt = kinds[dom]
     bytes_per_launch = table[dom] * N

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ in
 // store side hit at most two threads per bank.
 constexpr int kTileV = 64;
 
-__global__ void __launch_bounds__(256) transpose4_kernel(const float* __restrict__ in,
+__global__ void __launch_bounds__(256, 6) transpose4_kernel(const float* __restrict__ in,
                                                          float* __restrict__ out, int R, int C,
                                                          const float* __restrict__ w, double* part,
                                                          const int* done)

@@ -140,7 +140,7 @@ size_t poisson_bytes(const Grid& g, int eb)
 size_t solve_bytes(const Grid& g, int eb, int max_iter)
 {
     return poisson_bytes(g, eb) + up256(sizeof(double) * 3 * ((size_t)max_iter + 1)) +
-           (transposed_axis1(g, eb) ? 5 : 4) * up256((size_t)eb * g.N);
+           (transposed_axis1(g, eb) ? 7 : 4) * up256((size_t)eb * g.N);
 }
 
 void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Workspace* w, bool fields)
@@ -161,10 +161,15 @@ void carve(const Grid& g, int eb, int max_iter, unsigned char* base, Workspace* 
         w->nu_n = p; p += up256((size_t)eb * g.N);
         w->tmp = p;  p += up256((size_t)eb * g.N);
         w->rho = p;  p += up256((size_t)eb * g.N);
-        w->xt = nullptr;
-        if (transposed_axis1(g, eb)) { w->xt = p; p += up256((size_t)eb * g.N); }
+        w->xt = w->mu_t = w->nu_t = nullptr;
+        if (transposed_axis1(g, eb)) {
+            w->xt = p;   p += up256((size_t)eb * g.N);
+            w->mu_t = p; p += up256((size_t)eb * g.N);
+            w->nu_t = p; p += up256((size_t)eb * g.N);
+        }
     } else {
-        w->logs = nullptr; w->mu_n = w->nu_n = w->tmp = w->rho = w->xt = nullptr;
+        w->logs = nullptr;
+        w->mu_n = w->nu_n = w->tmp = w->rho = w->xt = w->mu_t = w->nu_t = nullptr;
     }
     w->bytes = (size_t)(p - base);
 }
@@ -296,6 +301,30 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
     return BFM_OK;
 }
 
+// c-transform out = src^c that leaves its output transposed: the sweep along
+// the rows of src (with the dot of src and w_src on load), one transpose,
+// then the sweep along the rows of the transposed field in place (with the
+// dot of out and w_out on store; w_out is laid out like out).  2-D quadratic
+// cost only; one transpose instead of the two of ct_with_dots.
+template <typename T>
+static bfm_status ct_flip(const Grid& g, const T* src, T* out, const T* w_src, const T* w_out,
+                          double* p_in, int* n_in, double* p_out, int* n_out, const int* done,
+                          cudaStream_t st, T* scratch)
+{
+    bfm_status s;
+    {
+        ProfScope ps(PK_CT0, 1, st);
+        s = launch_ct_pass<T>(g, 0, src, scratch, true, w_src, p_in, nullptr, nullptr, done,
+                              kMaxPartials, st, n_in);
+        if (s != BFM_OK) return s;
+    }
+    s = transpose<T>(g, true, scratch, out, nullptr, nullptr, nullptr, done, st);
+    if (s != BFM_OK) return s;
+    ProfScope ps(PK_CT1, 1, st);
+    return launch_ct_pass<T>(transposed_grid(g), 0, out, out, false, nullptr, nullptr, w_out, p_out,
+                             done, kMaxPartials, st, n_out);
+}
+
 // Forward transforms of f = base - in up to (and including) the middle pass;
 // the spectrum of g stays in `buf`.  G partials go to p_g.
 // With xt (2-D, long columns) the middle pass runs along the rows of a
@@ -358,6 +387,74 @@ static bfm_status poisson_inverse(const Grid& g, const AxisTables* tabs, T* buf,
 // thousand: one per CTA of the launch that produced them)
 constexpr int kFinThreads = 1024;
 
+// The half step on 2-D grids with long columns (quadratic cost): phi is kept
+// in the grid's layout and psi in the transposed one, so the c-transforms
+// phi -> psi and psi -> phi each leave their output transposed (ct_flip, one
+// transpose) and the psi-half runs on the transposed grid with the
+// transposed copies of mu and nu; the c-transform before each Poisson solve
+// keeps its layout (its output feeds the pushforward and the update of the
+// same potential).  Same steps, dots and step rule as half_step.
+template <typename T>
+static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half, T* phi, T* psi,
+                                    Logs logs, cudaStream_t st)
+{
+    const double hd = 1.0 / (double)g0.N;
+    const int* done = &w->state->done;
+    const Grid gt = transposed_grid(g0);
+    const Grid& g = phi_half ? g0 : gt;                  // layout of this half's potential
+    const AxisTables swapped[3] = {w->tabs[1], w->tabs[0], w->tabs[2]};
+    const AxisTables* tabs = phi_half ? w->tabs : swapped;
+    T* mu = (T*)(phi_half ? w->mu_n : w->mu_t);          // mu and nu in the layout of g
+    T* nu = (T*)(phi_half ? w->nu_n : w->nu_t);
+    T* mu_o = (T*)(phi_half ? w->mu_t : w->mu_n);        // ... and in the other layout
+    T* nu_o = (T*)(phi_half ? w->nu_t : w->nu_n);
+    T* tmp = (T*)w->tmp;
+    T* rho = (T*)w->rho;
+    T* xt = (T*)w->xt;
+    T* xg = transposed_axis1(g, (int)sizeof(T)) ? xt : nullptr;
+    T* src = phi_half ? phi : psi;
+    T* dst = phi_half ? psi : phi;
+    const T* w_src = phi_half ? nu : mu;
+    const T* w_dst = phi_half ? mu : nu;
+    const T* w_dst_o = phi_half ? mu_o : nu_o;
+    const T* source = phi_half ? mu : nu;
+    const T* target = phi_half ? nu : mu;
+    int ni = 0, no = 0, ng = 0;
+    bfm_status s;
+    s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xg,
+                        nullptr);
+    if (s != BFM_OK) return s;
+    {
+        ProfScope ps(PK_SMALL, 1, st);
+        finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+                                                        phi_half ? 0 : 2, logs);
+        BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    }
+    {
+        ProfScope ps(PK_PUSH, 1, st);
+        s = launch_pushforward<T>(g, tmp, source, rho, done, st, nullptr);
+        if (s != BFM_OK) return s;
+    }
+    s = poisson_forward<T>(g, tabs, rho, target, rho, slot(w, 2), &ng, done, st, xg);
+    if (s != BFM_OK) return s;
+    {
+        ProfScope ps(PK_SMALL, 1, st);
+        finalize_G_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 2), ng, phi_half ? 0 : 1, logs);
+        BFM_LAUNCH_CHECK("finalize_G_kernel");
+    }
+    s = poisson_inverse<T>(g, tabs, rho, src, src, &w->state->sigma, done, st);
+    if (s != BFM_OK) return s;
+    s = ct_flip<T>(g, src, dst, w_src, w_dst_o, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
+    if (s != BFM_OK) return s;
+    {
+        ProfScope ps(PK_SMALL, 1, st);
+        finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
+                                                        phi_half ? 1 : 3, logs);
+        BFM_LAUNCH_CHECK("finalize_dual_kernel");
+    }
+    return BFM_OK;
+}
+
 template <typename T>
 bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
                             Logs logs, cudaStream_t st, const double* pc)
@@ -378,6 +475,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     int ni = 0, no = 0, ng = 0;
     bfm_status s;
     T* xt = (T*)w->xt;
+    if (w->mu_t && !pc) return half_step_flipped<T>(g, w, phi_half, phi, psi, logs, st);
     s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc);
     if (s != BFM_OK) return s;
     {
@@ -520,6 +618,12 @@ bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int ma
     scale_kernel<T><<<nb, th, 0, st>>>(mu, (T*)w.mu_n, g.N, w.state, 0);
     scale_kernel<T><<<nb, th, 0, st>>>(nu, (T*)w.nu_n, g.N, w.state, 1);
     BFM_LAUNCH_CHECK("scale_kernel");
+    if (w.mu_t) {
+        s = transpose<T>(g, true, (const T*)w.mu_n, (T*)w.mu_t, nullptr, nullptr, nullptr, nullptr, st);
+        if (s != BFM_OK) return s;
+        s = transpose<T>(g, true, (const T*)w.nu_n, (T*)w.nu_t, nullptr, nullptr, nullptr, nullptr, st);
+        if (s != BFM_OK) return s;
+    }
     const double* pc = cost_exponents(&o);
     init_state_kernel<<<1, 1, 0, st>>>(w.state, o.sigma0, tol, max_iter, o.beta1, o.beta2,
                                        o.alpha1, o.alpha2, o.sigma_min, pc ? 1 : 0,

@@ -47,6 +47,8 @@ struct Workspace {
     void* rho;
     void* xt;                 // transposed copy for axis-1 sweeps of 2-D grids with
                               // long columns (transposed_axis1), else NULL
+    void* mu_t;               // with xt: mu_n and nu_n transposed (the psi-half of a
+    void* nu_t;               // step runs on the transposed grid), else NULL
     size_t bytes;
 };
 
