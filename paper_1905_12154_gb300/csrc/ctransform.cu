@@ -870,6 +870,7 @@ int pick_K(int n)
     if (n <= 64) return 2;
     if (n <= 128) return 4;
     if (n <= 256) return 8;
+    if (n == 384) return 12;      // 32 chunks: no idle lane in the line's warp
     return 16;
 }
 
@@ -911,6 +912,7 @@ void* select_kernel(int K, bool contig, bool batched)
         case 2: return kernel_for<T, 2>(contig, batched);
         case 4: return kernel_for<T, 4>(contig, batched);
         case 8: return kernel_for<T, 8>(contig, batched);
+        case 12: return kernel_for<T, 12>(contig, batched);
         default: return kernel_for<T, 16>(contig, batched);
     }
 }
@@ -924,7 +926,11 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
     p.K = pick_K(n);
     p.G = next_pow2((n + p.K - 1) / p.K);
     const bool contig = (axis == 0);
-    const int chunks = (n + p.K - 1) / p.K + 1;
+    // pad words of the skewed layout: one per 2^lg cells (Skew<K>: lg = log2 of
+    // the largest power of two <= K), plus one
+    int lg = 0;
+    while ((2 << lg) <= p.K && lg < 5) ++lg;
+    const int chunks = (n >> lg) + 2;
     int LDI = n + 2 * chunks + 8;                         // skewed index stack (two shorts per chunk)
     LDI += LDI & 1;
     const int nf = n + chunks + 1;                        // skewed values (one word per chunk)

@@ -42,9 +42,11 @@ def host(t):
 
 # rows of more than 256 cells take the row kernel (one thread group per row,
 # 16 cells per thread below 1024, else 32): aligned, ragged (257, 300, 1500)
-# and unaligned (511, 1027) lengths, in 2-D and 3-D
+# and unaligned (511, 1027) lengths, in 2-D and 3-D; lines of 384 cells along
+# axes 1 and 2 take tiles of 12 cells per thread
 CT_SHAPES = [(2, 2), (7, 5), (64, 64), (33, 100), (257, 96), (48, 31, 20), (9, 40, 13),
-             (300, 5, 3), (511, 7), (1024, 3), (1500, 4), (1027, 3), (4096, 2)]
+             (300, 5, 3), (511, 7), (1024, 3), (1500, 4), (1027, 3), (4096, 2),
+             (6, 384, 32), (384, 4, 8), (3, 384)]
 
 
 @pytest.mark.parametrize("shape", CT_SHAPES, ids=str)
