@@ -1036,6 +1036,20 @@ static int ct_blocks(const CtPlan& p, int max_blocks)
     return (int)blocks;
 }
 
+int ct_pass_blocks(const Grid& g, int axis, int elem_bytes, int max_blocks)
+{
+    if (use_row_kernel(g, axis)) {
+        const CtPlan p = plan_ct_row(g, elem_bytes);
+        long long blocks = (p.tiles.nlines + p.W - 1) / p.W;
+        const long long cap = (long long)num_sms() * 2;      // two resident CTAs per SM
+        if (blocks > cap) blocks = cap;
+        if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
+        if (blocks < 1) blocks = 1;
+        return (int)blocks;
+    }
+    return ct_blocks(plan_ct_pass(g, axis, elem_bytes), max_blocks);
+}
+
 template <typename T>
 bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool negate,
                           const T* w_in, double* part_in, const T* w_out, double* part_out,
@@ -1047,11 +1061,7 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
                                       done);
         void* k = (p.K == 32) ? (void*)ct_row_kernel<T, 32> : (void*)ct_row_kernel<T, 16>;
         BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
-        long long blocks = (p.tiles.nlines + p.W - 1) / p.W;
-        const long long cap = (long long)num_sms() * 2;      // two resident CTAs per SM
-        if (blocks > cap) blocks = cap;
-        if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
-        if (blocks < 1) blocks = 1;
+        const int blocks = ct_pass_blocks(g, axis, (int)sizeof(T), max_blocks);
         void* args[] = {&a};
         BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(p.threads), args, p.smem, st));
         if (blocks_used) *blocks_used = (int)blocks;
@@ -1061,7 +1071,7 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
     CtArgs<T> a = make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out, done);
     void* k = select_kernel<T>(p.K, axis == 0, false);
     BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
-    const int blocks = ct_blocks(p, max_blocks);
+    const int blocks = ct_pass_blocks(g, axis, (int)sizeof(T), max_blocks);
     const CtArgs<T>* none = nullptr;
     void* args[] = {&a, &none};
     BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(p.threads), args, p.smem, st));

@@ -38,6 +38,8 @@ struct DctPlan {
 CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes);
 DctPlan plan_dct_pass(const Grid& g, int axis, int elem_bytes);
 
+// number of CTAs (= partial sums) launch_ct_pass uses for this pass
+int ct_pass_blocks(const Grid& g, int axis, int elem_bytes, int max_blocks);
 template <typename T>
 bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool negate,
                           const T* w_in, double* part_in, const T* w_out, double* part_out,

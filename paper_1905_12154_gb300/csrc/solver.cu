@@ -97,6 +97,7 @@ __global__ void init_state_kernel(SolverState* st, double sigma0, double tol, in
     st->done = 0;
     st->converged = 0;
     st->nonfinite = 0;
+    st->pend = 0;
     st->J_old = 0.0;
     st->G = 0.0;
     st->last_resid = 0.0;
@@ -110,6 +111,29 @@ __global__ void finalize_dual_kernel(SolverState* st, const double* pin, int nin
     const double a = block_sum_parts(pin, nin, red);
     const double b = block_sum_parts(pout, nout, red);
     if (threadIdx.x == 0) finalize_dual_body(st, hd * (a + b), mode, logs);
+}
+
+// Flipped layout (half_step_flipped): the c-transform that ends a half step
+// leaves its output's dot out, because the next half step's first sweep
+// reads that field with the same weight.  At the start of a half step the
+// sums of that sweep (pin) complete the previous half step's dual value
+// (with pprev, the dot of that half step's updated potential), whose step
+// rule runs first (mode 1 or 3), then the measurement of this one (pin + pout,
+// mode 0 or 2).  The first half step of a solve has nothing pending.
+__global__ void finalize_dual_pend_kernel(SolverState* st, const double* pprev, int nprev,
+                                          const double* pin, int nin, const double* pout, int nout,
+                                          double hd, int mode, Logs logs)
+{
+    if (st->done) return;
+    __shared__ double red[32];
+    const double a = block_sum_parts(pin, nin, red);
+    const double b = block_sum_parts(pout, nout, red);
+    const double c = st->pend ? block_sum_parts(pprev, nprev, red) : 0.0;
+    if (threadIdx.x == 0) {
+        if (st->pend) finalize_dual_body(st, hd * (c + a), mode == 0 ? 3 : 1, logs);
+        if (!st->done) finalize_dual_body(st, hd * (a + b), mode, logs);
+        st->pend = 1;
+    }
 }
 
 __global__ void finalize_G_kernel(SolverState* st, const double* part, int np, int mode, Logs logs)
@@ -303,13 +327,12 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
 
 // c-transform out = src^c that leaves its output transposed: the sweep along
 // the rows of src (with the dot of src and w_src on load), one transpose,
-// then the sweep along the rows of the transposed field in place (with the
-// dot of out and w_out on store; w_out is laid out like out).  2-D quadratic
-// cost only; one transpose instead of the two of ct_with_dots.
+// then the sweep along the rows of the transposed field in place.  2-D
+// quadratic cost only; one transpose instead of the two of ct_with_dots.  The
+// dot of the output is taken by the next sweep that reads it.
 template <typename T>
-static bfm_status ct_flip(const Grid& g, const T* src, T* out, const T* w_src, const T* w_out,
-                          double* p_in, int* n_in, double* p_out, int* n_out, const int* done,
-                          cudaStream_t st, T* scratch)
+static bfm_status ct_flip(const Grid& g, const T* src, T* out, const T* w_src, double* p_in,
+                          int* n_in, const int* done, cudaStream_t st, T* scratch)
 {
     bfm_status s;
     {
@@ -321,8 +344,8 @@ static bfm_status ct_flip(const Grid& g, const T* src, T* out, const T* w_src, c
     s = transpose<T>(g, true, scratch, out, nullptr, nullptr, nullptr, done, st);
     if (s != BFM_OK) return s;
     ProfScope ps(PK_CT1, 1, st);
-    return launch_ct_pass<T>(transposed_grid(g), 0, out, out, false, nullptr, nullptr, w_out, p_out,
-                             done, kMaxPartials, st, n_out);
+    return launch_ct_pass<T>(transposed_grid(g), 0, out, out, false, nullptr, nullptr, nullptr,
+                             nullptr, done, kMaxPartials, st, nullptr);
 }
 
 // Forward transforms of f = base - in up to (and including) the middle pass;
@@ -393,7 +416,11 @@ constexpr int kFinThreads = 1024;
 // transpose) and the psi-half runs on the transposed grid with the
 // transposed copies of mu and nu; the c-transform before each Poisson solve
 // keeps its layout (its output feeds the pushforward and the update of the
-// same potential).  Same steps, dots and step rule as half_step.
+// same potential).  The dual value after the update (J(phi_{n+1/2}) or
+// I(psi_{n+1})) shares its second term with the measurement that starts the
+// next half step (<psi_{n+1/2}, mu> or <phi_{n+1}, nu>), so its step rule runs
+// there (finalize_dual_pend_kernel), before the measurement and before the
+// next update uses sigma.  Same steps and step rule as half_step.
 template <typename T>
 static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half, T* phi, T* psi,
                                     Logs logs, cudaStream_t st)
@@ -406,8 +433,6 @@ static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half,
     const AxisTables* tabs = phi_half ? w->tabs : swapped;
     T* mu = (T*)(phi_half ? w->mu_n : w->mu_t);          // mu and nu in the layout of g
     T* nu = (T*)(phi_half ? w->nu_n : w->nu_t);
-    T* mu_o = (T*)(phi_half ? w->mu_t : w->mu_n);        // ... and in the other layout
-    T* nu_o = (T*)(phi_half ? w->nu_t : w->nu_n);
     T* tmp = (T*)w->tmp;
     T* rho = (T*)w->rho;
     T* xt = (T*)w->xt;
@@ -416,7 +441,6 @@ static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half,
     T* dst = phi_half ? psi : phi;
     const T* w_src = phi_half ? nu : mu;
     const T* w_dst = phi_half ? mu : nu;
-    const T* w_dst_o = phi_half ? mu_o : nu_o;
     const T* source = phi_half ? mu : nu;
     const T* target = phi_half ? nu : mu;
     int ni = 0, no = 0, ng = 0;
@@ -425,10 +449,13 @@ static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half,
                         nullptr);
     if (s != BFM_OK) return s;
     {
+        // the previous half step's flip swept the other layout's rows first
+        const int nprev = ct_pass_blocks(phi_half ? gt : g0, 0, (int)sizeof(T), kMaxPartials);
         ProfScope ps(PK_SMALL, 1, st);
-        finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
-                                                        phi_half ? 0 : 2, logs);
-        BFM_LAUNCH_CHECK("finalize_dual_kernel");
+        finalize_dual_pend_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 3), nprev, slot(w, 0),
+                                                             ni, slot(w, 1), no, hd,
+                                                             phi_half ? 0 : 2, logs);
+        BFM_LAUNCH_CHECK("finalize_dual_pend_kernel");
     }
     {
         ProfScope ps(PK_PUSH, 1, st);
@@ -444,15 +471,7 @@ static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half,
     }
     s = poisson_inverse<T>(g, tabs, rho, src, src, &w->state->sigma, done, st);
     if (s != BFM_OK) return s;
-    s = ct_flip<T>(g, src, dst, w_src, w_dst_o, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt);
-    if (s != BFM_OK) return s;
-    {
-        ProfScope ps(PK_SMALL, 1, st);
-        finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w->state, slot(w, 0), ni, slot(w, 1), no, hd,
-                                                        phi_half ? 1 : 3, logs);
-        BFM_LAUNCH_CHECK("finalize_dual_kernel");
-    }
-    return BFM_OK;
+    return ct_flip<T>(g, src, dst, w_src, slot(w, 3), &ni, done, st, xt);
 }
 
 template <typename T>

@@ -23,6 +23,8 @@ struct SolverState {
     int done;
     int converged;
     int nonfinite;
+    int pend;                 // the previous half step's step rule awaits its dual
+                              // value (flipped layout: see finalize_dual_pend_kernel)
     int power;                // separable power cost with exponents cost_p
     double cost_p[3];
 };
