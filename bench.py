@@ -49,11 +49,12 @@ BYTES_PER_CELL_2D = {
 # copy.  The row sweep then reads and writes (8 bytes); the dual dot of the
 # c-transform output moves into the transpose back, so of the 12 transposes of
 # an iteration 4 read a weight as well (8 x 8 + 4 x 12 bytes).
-# Long columns: the axis-1 sweep runs on a transposed copy.  Of the L
-# transposes per iteration, 4 belong to the two Poisson solves and one to each
-# c-transform; a c-transform with a second one (back to its input's layout)
-# takes the dot of its output there (L - 8 of them), the others (12 - L) leave
-# their output transposed and take that dot in the second sweep's store.
+# Long columns: the second sweep of a c-transform runs along rows of a
+# transposed field and takes no dot (read, write).  Of the L transposes per
+# iteration, 4 belong to the two Poisson solves and one to each c-transform;
+# a c-transform with a second one (back to its input's layout) takes the dot
+# of its output there (L - 8 of them); the others leave their output
+# transposed and its dot to the next sweep that reads it.
 BYTES_PER_CELL_2D_TRANSPOSED = dict(BYTES_PER_CELL_2D, ct_pass_axis1=8)
 
 
@@ -62,21 +63,19 @@ def transpose_bytes_per_cell(launches_per_iter: float) -> float:
     return (dots * 12 + (launches_per_iter - dots) * 8) / launches_per_iter
 
 
-def second_sweep_bytes_per_cell(transposes_per_iter: float) -> float:
-    flips = 12 - transposes_per_iter
-    return (8 * (4 - flips) + 12 * flips) / 4
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # of the launches of that kind in one cold-cache ncu capture, summarised in
 # profiles/ct_row_kernel_annulus5g_4096_fp32.md); reported only while the
 # kernel source still matches the one the counters were taken on
 TRAFFIC = {
-    "ct_pass_axis1": {"bytes": (67152128 + 12175360 + 67152128 + 11724544 + 67151616 + 11663104) / 3,
+    # second sweeps (rows of a transposed field, no dot): launches 1 and 11 of the capture
+    "ct_pass_axis1": {"bytes": (67151616 + 11848960 + 67151616 + 11812608) / 2,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "b21829bb781637a54a813197e5ec887f5cc2c3e8c473fe169f06b12dab4c6c0f"},
-    "ct_pass_axis0": {"bytes": (134998784 + 25938688 + 135831808 + 27668224 + 134494976 + 25831936 +
-                                135936768 + 28055552) / 4,
+                      "sha256": "90773cf7f0042c05fb4e07e9d7f8d337ae800dc3a6b68393ca7037651b24c9cb"},
+    # first sweeps (with the dual dot on load): launches 9 and 12
+    "ct_pass_axis0": {"bytes": (134396416 + 26396416 + 136529920 + 27986688) / 2,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "b21829bb781637a54a813197e5ec887f5cc2c3e8c473fe169f06b12dab4c6c0f"},
+                      "sha256": "90773cf7f0042c05fb4e07e9d7f8d337ae800dc3a6b68393ca7037651b24c9cb"},
 }
 
 
@@ -395,8 +394,7 @@ def main():
     table = BYTES_PER_CELL_2D
     if kinds.get("transpose", (0, 0))[1]:
         lt = kinds["transpose"][1] / prof_steps
-        table = dict(BYTES_PER_CELL_2D_TRANSPOSED, transpose=transpose_bytes_per_cell(lt),
-                     ct_pass_axis1=second_sweep_bytes_per_cell(lt))
+        table = dict(BYTES_PER_CELL_2D_TRANSPOSED, transpose=transpose_bytes_per_cell(lt))
     dom = max((k for k in kinds if k in table and kinds[k][1]), key=lambda k: kinds[k][0])
     ms, cnt = kinds[dom]
     bytes_per_launch = table[dom] * N
