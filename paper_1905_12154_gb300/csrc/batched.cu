@@ -246,25 +246,54 @@ static bfm_status enqueue_half(const ClassPlan& c, unsigned char* wsp, int h, cu
     return BFM_OK;
 }
 
+struct BatchStreams;
 template <typename T>
 static bfm_status solve_batched_body(int nprob, const void* const* mu, const void* const* nu,
                                      BatchPlan& bp, double tol, int max_iter, const bfm_options& o,
-                                     unsigned char* wsp, cudaStream_t st, bfm_result* outs);
+                                     unsigned char* wsp, BatchStreams& bs, bfm_result* outs);
 
 // The caller's stream may be the legacy default stream, which cannot be
 // captured into a graph: the solve runs on a private stream once the caller's
 // earlier work (the inputs) is complete, and is complete itself on return.
+// Private streams of one batched solve: the main one and one per class of
+// grid shape (the classes' chains are independent and run as parallel
+// branches of the captured graph).
+struct BatchStreams {
+    cudaStream_t main = nullptr;
+    std::vector<cudaStream_t> cls;
+    std::vector<cudaEvent_t> ev;              // [0]: fork, [1 + c]: join of class c
+    ~BatchStreams()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (cudaStream_t c : cls) cudaStreamDestroy(c);
+        if (main) cudaStreamDestroy(main);
+    }
+    bfm_status create(size_t nclass)
+    {
+        BFM_CUDA(cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking));
+        cls.assign(nclass, nullptr);
+        ev.assign(nclass + 1, nullptr);
+        for (size_t c = 0; c < nclass; ++c) BFM_CUDA(cudaStreamCreateWithFlags(&cls[c], cudaStreamNonBlocking));
+        for (size_t i = 0; i <= nclass; ++i) BFM_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+        return BFM_OK;
+    }
+};
+
 template <typename T>
 static bfm_status solve_batched_impl(int nprob, const void* const* mu, const void* const* nu,
                                      BatchPlan& bp, double tol, int max_iter, const bfm_options& o,
                                      unsigned char* wsp, cudaStream_t user, bfm_result* outs)
 {
     BFM_CUDA(cudaStreamSynchronize(user));
-    cudaStream_t st;
-    BFM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    bfm_status s = solve_batched_body<T>(nprob, mu, nu, bp, tol, max_iter, o, wsp, st, outs);
-    cudaError_t e = cudaStreamSynchronize(st);
-    cudaStreamDestroy(st);
+    bfm_status s;
+    cudaError_t e;
+    {
+        BatchStreams bs;
+        s = bs.create(bp.classes.size());
+        if (s != BFM_OK) return s;
+        s = solve_batched_body<T>(nprob, mu, nu, bp, tol, max_iter, o, wsp, bs, outs);
+        e = cudaStreamSynchronize(bs.main);
+    }
     if (s == BFM_OK && e != cudaSuccess) return cuda_status(e, "batched solve");
     return s;
 }
@@ -272,8 +301,9 @@ static bfm_status solve_batched_impl(int nprob, const void* const* mu, const voi
 template <typename T>
 static bfm_status solve_batched_body(int nprob, const void* const* mu, const void* const* nu,
                                      BatchPlan& bp, double tol, int max_iter, const bfm_options& o,
-                                     unsigned char* wsp, cudaStream_t st, bfm_result* outs)
+                                     unsigned char* wsp, BatchStreams& bs, bfm_result* outs)
 {
+    cudaStream_t st = bs.main;
     bfm_status s;
     for (int p = 0; p < nprob; ++p) {
         s = init_impl<T>((const T*)mu[p], (const T*)nu[p], bp.grids[p], tol, max_iter, o,
@@ -296,14 +326,20 @@ static bfm_status solve_batched_body(int nprob, const void* const* mu, const voi
     const int chunk = o.poll_every > 0 ? o.poll_every : 4;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // one captured chunk: each class's iterations on its own stream, forked
+    // from and joined back to the main stream (parallel graph branches)
     BFM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     bfm_status cap = BFM_OK;
-    for (int it = 0; it < chunk && cap == BFM_OK; ++it)
-        for (int h = 0; h < 2 && cap == BFM_OK; ++h)
-            for (const ClassPlan& c : bp.classes) {
-                cap = enqueue_half<T>(c, wsp, h, st);
-                if (cap != BFM_OK) break;
-            }
+    cudaError_t ce = cudaEventRecord(bs.ev[0], st);
+    for (size_t ci = 0; ci < bp.classes.size() && cap == BFM_OK && ce == cudaSuccess; ++ci) {
+        cudaStream_t cs = bs.cls[ci];
+        ce = cudaStreamWaitEvent(cs, bs.ev[0], 0);
+        for (int it = 0; it < chunk && cap == BFM_OK && ce == cudaSuccess; ++it)
+            for (int h = 0; h < 2 && cap == BFM_OK; ++h) cap = enqueue_half<T>(bp.classes[ci], wsp, h, cs);
+        if (ce == cudaSuccess) ce = cudaEventRecord(bs.ev[1 + ci], cs);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, bs.ev[1 + ci], 0);
+    }
+    if (cap == BFM_OK && ce != cudaSuccess) cap = cuda_status(ce, "batched capture fork/join");
     cudaError_t e = cudaStreamEndCapture(st, &graph);      // always ends the capture
     if (cap != BFM_OK) { if (graph) cudaGraphDestroy(graph); return cap; }
     if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
