@@ -80,6 +80,7 @@ struct ClassPlan {
     size_t inv[2][3];
     size_t push[2];
     int nin, nout, ng;
+    bool rows16 = false;        // every problem's phi and psi 16-byte aligned (workspace fields are)
 };
 
 struct BatchPlan {
@@ -226,15 +227,15 @@ static bfm_status enqueue_half(const ClassPlan& c, unsigned char* wsp, int h, cu
     s = launch_pushforward_batched<T>(d, g.N, n, wsp + c.push[h], st);
     if (s != BFM_OK) return s;
     for (int a = 0; a < d - 1; ++a) {
-        s = launch_dct_pass_batched<T>(g, a, PASS_FWD, n, wsp + c.fwd[h][a], st);
+        s = launch_dct_pass_batched<T>(g, a, PASS_FWD, n, wsp + c.fwd[h][a], st, c.rows16);
         if (s != BFM_OK) return s;
     }
-    s = launch_dct_pass_batched<T>(g, d - 1, PASS_MID, n, wsp + c.mid[h], st);
+    s = launch_dct_pass_batched<T>(g, d - 1, PASS_MID, n, wsp + c.mid[h], st, c.rows16);
     if (s != BFM_OK) return s;
     finalize_G_batched<<<n, 256, 0, st>>>(fin, c.ng, h ? 1 : 0);
     BFM_LAUNCH_CHECK("finalize_G_batched");
     for (int a = d - 2; a >= 0; --a) {
-        s = launch_dct_pass_batched<T>(g, a, PASS_INV, n, wsp + c.inv[h][a], st);
+        s = launch_dct_pass_batched<T>(g, a, PASS_INV, n, wsp + c.inv[h][a], st, c.rows16);
         if (s != BFM_OK) return s;
     }
     for (int a = 0; a < d; ++a) {
@@ -314,6 +315,10 @@ static bfm_status solve_batched_body(int nprob, const void* const* mu, const voi
         c.nin = ct_batch_blocks<T>(c.g, 0);
         c.nout = ct_batch_blocks<T>(c.g, c.g.ndim - 1);
         c.ng = dct_batch_blocks<T>(c.g, c.g.ndim - 1);
+        c.rows16 = true;
+        for (int p : c.probs)
+            if ((reinterpret_cast<uintptr_t>(outs[p].phi) | reinterpret_cast<uintptr_t>(outs[p].psi)) & 15u)
+                c.rows16 = false;
     }
     std::vector<unsigned char> host;
     s = build_args<T>(bp, wsp, outs, max_iter, host);

@@ -622,9 +622,11 @@ __device__ __forceinline__ void group_sync(int w, int G)
     else asm volatile("bar.sync %0, %1;" :: "r"(1 + w), "r"(G) : "memory");
 }
 
-template <typename T, int K>
-__global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a)
+// BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
+template <typename T, int K, bool BATCHED>
+__global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtArgs<T>* batch)
 {
+    const CtArgs<T>& a = BATCHED ? batch[blockIdx.y] : a0;
     if (a.done && *a.done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SK = Skew<K>;
@@ -1059,10 +1061,11 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
         CtPlan p = plan_ct_row(g, (int)sizeof(T));
         CtArgs<T> a = make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out,
                                       done);
-        void* k = (p.K == 32) ? (void*)ct_row_kernel<T, 32> : (void*)ct_row_kernel<T, 16>;
+        void* k = (p.K == 32) ? (void*)ct_row_kernel<T, 32, false> : (void*)ct_row_kernel<T, 16, false>;
         BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
         const int blocks = ct_pass_blocks(g, axis, (int)sizeof(T), max_blocks);
-        void* args[] = {&a};
+        const CtArgs<T>* none = nullptr;
+        void* args[] = {&a, &none};
         BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(p.threads), args, p.smem, st));
         if (blocks_used) *blocks_used = (int)blocks;
         return BFM_OK;
@@ -1084,7 +1087,7 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
 template <typename T>
 int ct_batch_blocks(const Grid& g, int axis)
 {
-    return ct_blocks(plan_ct_pass(g, axis, (int)sizeof(T)), kMaxPartials);
+    return ct_pass_blocks(g, axis, (int)sizeof(T), kMaxPartials);
 }
 
 template <typename T>
@@ -1092,7 +1095,7 @@ void fill_ct_batch_args(const Grid& g, int axis, const T* in, T* out, bool negat
                         double* part_in, const T* w_out, double* part_out, const int* done,
                         void* host_slot)
 {
-    CtPlan p = plan_ct_pass(g, axis, (int)sizeof(T));
+    CtPlan p = use_row_kernel(g, axis) ? plan_ct_row(g, (int)sizeof(T)) : plan_ct_pass(g, axis, (int)sizeof(T));
     *reinterpret_cast<CtArgs<T>*>(host_slot) =
         make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out, done);
 }
@@ -1103,6 +1106,20 @@ template <typename T>
 bfm_status launch_ct_pass_batched(const Grid& g, int axis, int nprob, const void* dev_args,
                                   cudaStream_t st)
 {
+    if (use_row_kernel(g, axis)) {
+        // long rows: the row kernel, one grid row per problem
+        const CtPlan p = plan_ct_row(g, (int)sizeof(T));
+        void* k = (p.K == 32) ? (void*)ct_row_kernel<T, 32, true> : (void*)ct_row_kernel<T, 16, true>;
+        BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+        const int blocks = ct_pass_blocks(g, axis, (int)sizeof(T), kMaxPartials);
+        CtArgs<T> dummy;
+        memset(&dummy, 0, sizeof(dummy));
+        const CtArgs<T>* batch = reinterpret_cast<const CtArgs<T>*>(dev_args);
+        void* args[] = {&dummy, &batch};
+        BFM_CUDA(cudaLaunchKernel(k, dim3((unsigned)blocks, (unsigned)nprob), dim3(p.threads), args,
+                                  p.smem, st));
+        return BFM_OK;
+    }
     CtPlan p = plan_ct_pass(g, axis, (int)sizeof(T));
     void* k = select_kernel<T>(p.K, axis == 0, true);
     BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));

@@ -840,12 +840,14 @@ constexpr int dct_row_ctas(int mode, int logn)
     return mode == DCT_FWD ? 3 : mode == DCT_INV ? 3 : (logn == 12 ? 4 : 2);
 }
 
-template <int MODE, int LOGN>
+// BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
+template <int MODE, int LOGN, bool BATCHED>
 __global__ void __launch_bounds__((1 << LOGN) / 16, dct_row_ctas(MODE, LOGN) * (4096 >> LOGN))
-dct_row_kernel(DctArgs<float> a)
+dct_row_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
 {
     using C = float2;
     constexpr int n = 1 << LOGN, T = n / 16, NQ = n / 4, QPT = NQ / T;   // QPT = 4 float4 per row
+    const DctArgs<float>& a = BATCHED ? batch[blockIdx.y] : a0;
     if (a.done && *a.done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* z = reinterpret_cast<C*>(smem_raw);
@@ -1557,26 +1559,32 @@ static void* select_dct(int mode, int elem_bytes, bool contig, bool batched, boo
     return dct_kernel<double, DCT_INV>(contig, batched);
 }
 
-// The compile-time row kernel for FP32 rows of 1024-4096 cells whose fields
+template <int LOGN, bool BATCHED>
+static void* dct_row_of(int mode)
+{
+    return mode == DCT_FWD ? (void*)dct_row_kernel<DCT_FWD, LOGN, BATCHED>
+         : mode == DCT_MID ? (void*)dct_row_kernel<DCT_MID, LOGN, BATCHED>
+                           : (void*)dct_row_kernel<DCT_INV, LOGN, BATCHED>;
+}
+
+// The compile-time row kernel for FP32 rows of 512-4096 cells whose fields
 // are 16-byte aligned (float4 rows); the middle pass only on 2-D grids (its
 // eigenvalue of the line comes from the one other axis).  NULL: the general
 // kernel handles the pass.
-static void* select_dct_row(int mode, int n, int ndim, const void* in, const void* base,
-                            const void* out, const void* upd)
+static void* select_dct_row(int mode, int n, int ndim, bool batched)
+{
+    if (mode == DCT_MID && ndim != 2) return nullptr;
+    if (n == 4096) return batched ? dct_row_of<12, true>(mode) : dct_row_of<12, false>(mode);
+    if (n == 2048) return batched ? dct_row_of<11, true>(mode) : dct_row_of<11, false>(mode);
+    if (n == 1024) return batched ? dct_row_of<10, true>(mode) : dct_row_of<10, false>(mode);
+    if (n == 512) return batched ? dct_row_of<9, true>(mode) : dct_row_of<9, false>(mode);
+    return nullptr;
+}
+
+static bool rows_aligned16(const void* in, const void* base, const void* out, const void* upd)
 {
     auto al = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
-    if (!al(in) || !al(base) || !al(out) || !al(upd)) return nullptr;
-    if (mode == DCT_MID && ndim != 2) return nullptr;
-    if (n == 4096)
-        return mode == DCT_FWD ? (void*)dct_row_kernel<DCT_FWD, 12>
-             : mode == DCT_MID ? (void*)dct_row_kernel<DCT_MID, 12> : (void*)dct_row_kernel<DCT_INV, 12>;
-    if (n == 2048)
-        return mode == DCT_FWD ? (void*)dct_row_kernel<DCT_FWD, 11>
-             : mode == DCT_MID ? (void*)dct_row_kernel<DCT_MID, 11> : (void*)dct_row_kernel<DCT_INV, 11>;
-    if (n == 1024)
-        return mode == DCT_FWD ? (void*)dct_row_kernel<DCT_FWD, 10>
-             : mode == DCT_MID ? (void*)dct_row_kernel<DCT_MID, 10> : (void*)dct_row_kernel<DCT_INV, 10>;
-    return nullptr;
+    return al(in) && al(base) && al(out) && al(upd);
 }
 
 static int dct_blocks(const DctPlan& p)
@@ -1625,8 +1633,8 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
             return BFM_OK;
         }
     }
-    if (sizeof(T) == 4 && axis == 0 && p.fast) {
-        void* rk = select_dct_row(mode, g.n[0], g.ndim, in, base, out, upd);
+    if (sizeof(T) == 4 && axis == 0 && p.fast && rows_aligned16(in, base, out, upd)) {
+        void* rk = select_dct_row(mode, g.n[0], g.ndim, false);
         if (rk) {
             // one line pair per CTA of n/16 threads, one resident wave
             const int threads = g.n[0] / 16;
@@ -1639,7 +1647,8 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
             if (blocks > cap) blocks = cap;
             if (blocks > kMaxPartials) blocks = kMaxPartials;
             if (blocks < 1) blocks = 1;
-            void* args[] = {&a};
+            const DctArgs<T>* none = nullptr;
+            void* args[] = {&a, &none};
             BFM_CUDA(cudaLaunchKernel(rk, dim3((unsigned)blocks), dim3(threads), args, smem, st));
             if (blocks_used) *blocks_used = (int)blocks;
             return BFM_OK;
@@ -1677,9 +1686,30 @@ bfm_status fill_dct_batch_args(const Grid& g, int axis, const AxisTables* tabs, 
 
 template <typename T>
 bfm_status launch_dct_pass_batched(const Grid& g, int axis, int mode, int nprob,
-                                   const void* dev_args, cudaStream_t st)
+                                   const void* dev_args, cudaStream_t st, bool rows16)
 {
     DctPlan p = plan_dct_pass(g, axis, (int)sizeof(T));
+    if (sizeof(T) == 4 && axis == 0 && p.fast && rows16) {
+        void* rk = select_dct_row(mode, g.n[0], g.ndim, true);
+        if (rk) {
+            const int threads = g.n[0] / 16;
+            const size_t smem = (size_t)p.LDZ * sizeof(float2);
+            BFM_CUDA(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int per_sm = 0;
+            BFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rk, threads, smem));
+            long long blocks = (p.tiles.nlines + 1) / 2;
+            const long long cap = (long long)num_sms() * (per_sm > 0 ? per_sm : 1);
+            if (blocks > cap) blocks = cap;
+            if (blocks < 1) blocks = 1;
+            DctArgs<float> dummy;
+            memset(&dummy, 0, sizeof(dummy));
+            const DctArgs<float>* batch = reinterpret_cast<const DctArgs<float>*>(dev_args);
+            void* args[] = {&dummy, &batch};
+            BFM_CUDA(cudaLaunchKernel(rk, dim3((unsigned)blocks, (unsigned)nprob), dim3(threads), args,
+                                      smem, st));
+            return BFM_OK;
+        }
+    }
     void* k = select_dct(mode, (int)sizeof(T), axis == 0, true, p.fast != 0);
     BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int blocks = dct_blocks(p);
@@ -1700,8 +1730,10 @@ template bfm_status fill_dct_batch_args<float>(const Grid&, int, const AxisTable
 template bfm_status fill_dct_batch_args<double>(const Grid&, int, const AxisTables*, const double*,
                                                 const double*, double*, const double*,
                                                 const double*, double*, const int*, void*);
-template bfm_status launch_dct_pass_batched<float>(const Grid&, int, int, int, const void*, cudaStream_t);
-template bfm_status launch_dct_pass_batched<double>(const Grid&, int, int, int, const void*, cudaStream_t);
+template bfm_status launch_dct_pass_batched<float>(const Grid&, int, int, int, const void*, cudaStream_t,
+                                                   bool);
+template bfm_status launch_dct_pass_batched<double>(const Grid&, int, int, int, const void*, cudaStream_t,
+                                                    bool);
 template bfm_status launch_dct_pass<float>(const Grid&, int, int, const AxisTables*, const float*,
                                            const float*, float*, const float*, const double*,
                                            double*, const int*, cudaStream_t, int*);

@@ -97,9 +97,10 @@ template <typename T>
 bfm_status fill_dct_batch_args(const Grid& g, int axis, const AxisTables* tabs, const T* in,
                                const T* base, T* out, const T* upd, const double* sigma,
                                double* part, const int* done, void* host_slot);
+// rows16: every problem's fields are 16-byte aligned (rows may move as float4)
 template <typename T>
 bfm_status launch_dct_pass_batched(const Grid& g, int axis, int mode, int nprob,
-                                   const void* dev_args, cudaStream_t st);
+                                   const void* dev_args, cudaStream_t st, bool rows16);
 size_t push_args_bytes(int elem_bytes);
 template <typename T>
 void fill_push_batch_args(const Grid& g, const T* psi, const T* mu, T* rho, const int* done,

@@ -81,6 +81,20 @@ def test_batched_fp32_uneven_sizes(B):
         assert abs(r["w2sq"] - ref["w2sq"]) / ref["w2sq"] < 1e-5
 
 
+def test_batched_fp32_long_rows(B):
+    """Sides of 512 and 1024: the batched forms of the c-transform's row kernel
+    and of the compile-time DCT row kernel; each problem as its own FP32 solve
+    and within 1e-5 of the FP64 oracle."""
+    probs = uneven_problems(3, (512, 1024), 35)
+    res = B.bfm_solve_batched([dev(m, torch.float32) for m, _ in probs],
+                              [dev(v, torch.float32) for _, v in probs], tol=0.0, max_iter=8)
+    for (m, v), r in zip(probs, res):
+        ref = oracle.solve(m, v, tol=0.0, max_iter=8)
+        assert abs(r["w2sq"] - ref["w2sq"]) / ref["w2sq"] < 1e-5
+        single = B.bfm_solve(dev(m, torch.float32), dev(v, torch.float32), tol=0.0, max_iter=8)
+        assert abs(r["w2sq"] - single["w2sq"]) / single["w2sq"] < 1e-6
+
+
 def test_batched_masks_stop_converged_problems(B):
     """A problem that converges early stops (its iteration count is its own)
     while a harder one keeps iterating in the same launches."""

@@ -115,10 +115,11 @@ def test_poisson_fp32(B, shape):
     assert abs(G_got - G_want) <= 2e-5 * abs(G_want)
 
 
-# Rows of 1024, 2048 and 4096 FP32 cells take the compile-time row kernel
+# Rows of 512 to 4096 FP32 cells take the compile-time row kernel
 # (float4 rows, one line pair per CTA); odd row counts leave a last pair with
 # one line.
-@pytest.mark.parametrize("shape", [(3, 4096), (16, 4096), (27, 2048), (48, 1024), (9, 1024)], ids=str)
+@pytest.mark.parametrize("shape", [(3, 4096), (16, 4096), (27, 2048), (48, 1024), (9, 1024), (9, 512)],
+                         ids=str)
 def test_poisson_fp32_long_rows(B, shape):
     f = si.random_field(shape, 7).astype(np.float32)
     g_want, G_want = oracle.poisson(f.astype(np.float64))
