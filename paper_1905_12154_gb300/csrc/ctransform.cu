@@ -612,6 +612,28 @@ __device__ void merge_pair_t(const T* f, const short* stk, short* beg, short* en
 constexpr int kRowMinN = 256;          // rows longer than this take the row kernel
 constexpr int kRowLongN = 1024;        // from here 32 cells per thread, else 16
 
+// First grid cell owned by parabola b, the successor of a on the envelope
+// (FP32): the two meet at s = (f_b - f_a) / (2 hh (j_b - j_a)) + (j_a + j_b)/2
+// and b is the lower one right of s, so the cell is ceil(s), clamped to
+// [0, n].  For neighbours j_b - j_a < 16 apart an error of the rounded s
+// moves at most values within a fraction of an ulp; for wider gaps, where
+// the two parabolas separate faster, the cell is confirmed by comparing the
+// evaluated parabolas at it and at the cell before (the comparison the
+// sequential sweep makes), which the rounded s misses by at most one cell.
+__device__ __forceinline__ int start_cell(float ja, float fa, float jb, float fb, float hh, int n)
+{
+    const float d = jb - ja;
+    const float q = __fdividef(fb - fa, (2.f * hh) * d);
+    const float s = fmaf(0.5f, ja + jb, q);
+    int c = (int)fminf(fmaxf(ceilf(s), 0.f), (float)n);
+    if (d >= 16.f && c > 0) {
+        const float x = (float)c;
+        if (c < n && !(parab_t(hh, x, jb, fb) <= parab_t(hh, x, ja, fa))) ++c;
+        else if (parab_t(hh, x - 1.f, jb, fb) <= parab_t(hh, x - 1.f, ja, fa)) --c;
+    }
+    return c;
+}
+
 static int row_cells_per_thread(int n) { return n >= kRowLongN ? 32 : 16; }
 
 // Barrier of one line group (G >= 32 threads, whole warps): a single warp
@@ -638,8 +660,13 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
     short* stk_all = reinterpret_cast<short*>(fs + (size_t)W * a.LD);
     short* seg_all = stk_all + (size_t)W * a.LDI;  // per group: beg[G], end[G], nzs[G]
     const int nwl = (G + 31) / 32;
+    const int nsw = (n + 31) >> 5;                 // words of one cell bit mask
+    // int scratch: per group 2 nwl scan words, 2 counts, then (FP32) the
+    // cell bit mask of owner starts and the list of writer masks
     int* wsum_all = reinterpret_cast<int*>(smem_raw + a.ioff);
-    int* cnt_all = wsum_all + W * nwl;
+    int* cnt_all = wsum_all + W * 2 * nwl;
+    unsigned* sw_all = reinterpret_cast<unsigned*>(cnt_all + 2 * W);
+    unsigned* wbm_all = sw_all + (size_t)W * nsw;
     __shared__ double red[32];
 
     const int tid = threadIdx.x;
@@ -650,7 +677,10 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
     short* beg = seg_all + (size_t)w * 3 * G;
     short* end = beg + G;
     short* nzs = end + G;
-    int* wsum = wsum_all + w * nwl;
+    int* wsum = wsum_all + w * 2 * nwl;
+    int* cnt = cnt_all + 2 * w;
+    unsigned* sw = sw_all + (size_t)w * nsw;
+    unsigned* wbm = wbm_all + (size_t)w * G;
     const T hh = a.hh;
     const int lo = t * K;
     const int hi = min(lo + K, n);
@@ -758,23 +788,179 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
             group_sync(w, G);
         }
         // ---- C: list of non-empty segments, in order ---------------------------
+        const bool ne = end[t] > beg[t];
+        int pos;
         {
-            const bool ne = end[t] > beg[t];
             // groups are whole warps (G >= 32)
             const unsigned mine = __ballot_sync(0xffffffffu, ne);
-            int pos = __popc(mine & ((1u << lane) - 1u));
+            pos = __popc(mine & ((1u << lane) - 1u));
+            if (sizeof(T) == 4)
+                for (int i = t; i < nsw; i += G) sw[i] = 0u;
             if (G > 32) {
                 if (lane == 0) wsum[t >> 5] = __popc(mine);
                 group_sync(w, G);
                 for (int i = 0; i < (t >> 5); ++i) pos += wsum[i];
             }
             if (ne) nzs[pos] = (short)t;
-            if (t == G - 1) cnt_all[w] = pos + (ne ? 1 : 0);
+            if (t == G - 1) cnt[0] = pos + (ne ? 1 : 0);
         }
         group_sync(w, G);
-        // ---- D: evaluate this thread's outputs, store, dual dot ----------------
+        // stores four outputs of this thread (float4 where the row allows) and
+        // adds them to the dual dot
+        T* dst = a.out + rb;
+        const T* wo = a.w_out ? a.w_out + rb : nullptr;
+        auto store4 = [&](int x0, const T* o) {
+            if (sizeof(T) == 4 && a.vec4 && x0 + 4 <= hi) {
+                float4 v4 = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
+                *reinterpret_cast<float4*>(dst + x0) = v4;
+                if (wo) {
+                    const float4 u4 = *reinterpret_cast<const float4*>(wo + x0);
+                    acc_t_out.add_prod(o[0], (T)u4.x); acc_t_out.add_prod(o[1], (T)u4.y);
+                    acc_t_out.add_prod(o[2], (T)u4.z); acc_t_out.add_prod(o[3], (T)u4.w);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (x0 + k < hi) {
+                        dst[x0 + k] = o[k];
+                        if (wo) acc_t_out.add_prod(o[k], wo[x0 + k]);
+                    }
+                }
+            }
+        };
+        bool walk = true;
+        if constexpr (sizeof(T) == 4) {
+            // ---- D (FP32): owners by rank, no sweep -------------------------------
+            // D1. every envelope parabola computes the first cell it owns from
+            // its predecessor (start_cell); along the envelope these cells do
+            // not decrease, and a parabola owns cells iff the next one starts
+            // later ("writer").  Writers set the bit of their start cell in the
+            // row's cell mask and their own bit in the thread's mask of stack
+            // positions.  A start that decreases (rounding between nearly
+            // collinear parabolas) sends the row to the sweep below.
+            bool bad = false;
+            unsigned bmask = 0u;
+            if (ne) {
+                const int M = cnt[0];
+                const int b0 = beg[t], e1 = end[t];
+                float jc = (float)stk[SK::s(b0)], fc = (float)f[SK::f(b0)];
+                int cc = 0;
+                if (pos > 0) {
+                    const int pp = end[nzs[pos - 1]] - 1;
+                    cc = start_cell((float)stk[SK::s(pp)], (float)f[SK::f(pp)], jc, fc, (float)hh, n);
+                }
+#pragma unroll 4
+                for (int p = b0 + 1; p < e1; ++p) {
+                    const float jn = (float)stk[SK::s(p)], fn = (float)f[SK::f(p)];
+                    const int cn = start_cell(jc, fc, jn, fn, (float)hh, n);
+                    bad |= cn < cc;
+                    if (cn > cc) {
+                        bmask |= 1u << (p - 1 - lo);
+                        atomicOr(&sw[cc >> 5], 1u << (cc & 31));
+                    }
+                    jc = jn; fc = fn; cc = cn;
+                }
+                int cn = n;
+                if (pos + 1 < M) {
+                    const int ps = beg[nzs[pos + 1]];
+                    cn = start_cell(jc, fc, (float)stk[SK::s(ps)], (float)f[SK::f(ps)], (float)hh, n);
+                }
+                bad |= cn < cc;
+                if (cn > cc) {
+                    bmask |= 1u << (e1 - 1 - lo);
+                    atomicOr(&sw[cc >> 5], 1u << (cc & 31));
+                }
+            }
+            walk = group_or(bad, w, G);            // also publishes the masks
+            if (!walk) {
+                // D2. the owner of cell x is the writer whose rank is the
+                // number of start bits at cells <= x, minus one.  One scan
+                // gives each thread the writers and starts before it (packed
+                // as two 16-bit counts); threads with writers are listed in
+                // order with their masks (nzs: thread, beg: writers before it).
+                const int nb = __popc(bmask);
+                unsigned sword = 0u;
+                if (lo < n) {
+                    sword = sw[lo >> 5];
+                    if (K < 32) sword = (sword >> (lo & 31)) & ((1u << K) - 1u);
+                }
+                const int v = (nb << 16) | __popc(sword);
+                int incl = v;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                const unsigned nzb = __ballot_sync(0xffffffffu, nb > 0);
+                int zpos = __popc(nzb & ((1u << lane) - 1u));
+                if (G > 32) {
+                    if (lane == 31) wsum[t >> 5] = incl;
+                    if (lane == 0) wsum[nwl + (t >> 5)] = __popc(nzb);
+                    group_sync(w, G);
+                    for (int i = 0; i < (t >> 5); ++i) { incl += wsum[i]; zpos += wsum[nwl + i]; }
+                }
+                const int excl = incl - v;
+                if (nb > 0) {
+                    nzs[zpos] = (short)t;
+                    beg[zpos] = (short)(excl >> 16);
+                    wbm[zpos] = bmask;
+                }
+                if (t == G - 1) cnt[1] = zpos + (nb > 0 ? 1 : 0);
+                group_sync(w, G);
+                if (lo < n) {
+                    const int Mw = cnt[1];
+                    const int R = (excl & 0xFFFF) + (int)(sword & 1u) - 1;
+                    int ml = 0, mh = Mw - 1;
+                    while (ml < mh) {
+                        const int mid = (ml + mh + 1) >> 1;
+                        if (beg[mid] <= R) ml = mid;
+                        else mh = mid - 1;
+                    }
+                    int m = ml;
+                    unsigned rem = wbm[m];
+                    for (int i = R - beg[m]; i > 0; --i) rem &= rem - 1u;
+                    int u = nzs[m];
+                    int pc = K * u + __ffs(rem) - 1;
+                    rem &= rem - 1u;
+                    float jc = (float)stk[SK::s(pc)], fc = (float)f[SK::f(pc)];
+                    // the next writer, loaded ahead of its start bit
+                    float jn = jc, fn = fc;
+                    auto load_next = [&]() {
+                        if (rem == 0u && m + 1 < Mw) {
+                            ++m;
+                            rem = wbm[m];
+                            u = nzs[m];
+                        }
+                        if (rem != 0u) {
+                            const int pn = K * u + __ffs(rem) - 1;
+                            rem &= rem - 1u;
+                            jn = (float)stk[SK::s(pn)];
+                            fn = (float)f[SK::f(pn)];
+                        }
+                    };
+                    load_next();
+                    float xf = (float)lo;
+                    for (int x0 = lo; x0 < hi; x0 += 4) {
+                        T o[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int xi = x0 + k - lo;
+                            if (xi > 0 && ((sword >> xi) & 1u)) {
+                                jc = jn; fc = fn;
+                                load_next();
+                            }
+                            o[k] = (T)parab_t((float)hh, xf, jc, fc);
+                            xf += 1.f;
+                        }
+                        store4(x0, o);
+                    }
+                }
+            }
+        }
+        if (walk) {
+        // ---- D: evaluate this thread's outputs by a sweep, store, dual dot -------
         if (lo < n) {
-            const int M = cnt_all[w];
+            const int M = cnt[0];
             const T xlo = (T)lo;
             int ml = 0, mh = M - 1;
             while (ml < mh) {
@@ -806,8 +992,6 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
             bool has_n = pn >= 0;
             T jn = (T)0, fn = (T)0;
             if (has_n) { jn = (T)stk[SK::s(pn)]; fn = f[SK::f(pn)]; }
-            T* dst = a.out + rb;
-            const T* wo = a.w_out ? a.w_out + rb : nullptr;
             T xf = xlo;
             for (int x0 = lo; x0 < hi; x0 += 4) {
                 T o[4];
@@ -828,24 +1012,9 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
                     o[k] = vc;
                     xf += (T)1;
                 }
-                if (sizeof(T) == 4 && a.vec4 && x0 + 4 <= hi) {
-                    float4 v4 = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
-                    *reinterpret_cast<float4*>(dst + x0) = v4;
-                    if (wo) {
-                        const float4 u4 = *reinterpret_cast<const float4*>(wo + x0);
-                        acc_t_out.add_prod(o[0], (T)u4.x); acc_t_out.add_prod(o[1], (T)u4.y);
-                        acc_t_out.add_prod(o[2], (T)u4.z); acc_t_out.add_prod(o[3], (T)u4.w);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (x0 + k < hi) {
-                            dst[x0 + k] = o[k];
-                            if (wo) acc_t_out.add_prod(o[k], wo[x0 + k]);
-                        }
-                    }
-                }
+                store4(x0, o);
             }
+        }
         }
         acc_in += acc_t_in.take();
         acc_out += acc_t_out.take();
@@ -992,8 +1161,11 @@ static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
     p.LDI = n + 2 * chunks + 8;
     p.LDI += p.LDI & 1;
     const int nwl = (p.G + 31) / 32;
+    // int scratch per group: 2 nwl scan words and 2 counts; FP32 rows add the
+    // cell mask of owner starts (one bit per cell) and G writer masks
+    const size_t ints = 2 * (size_t)nwl + 2 + (elem_bytes == 4 ? (size_t)((n + 31) >> 5) + p.G : 0);
     const size_t line_bytes = (size_t)p.LD * elem_bytes + (size_t)p.LDI * 2 + 3 * (size_t)p.G * 2 +
-                              4 * (size_t)nwl + 4;
+                              4 * ints;
     int W = 512 / p.G;
     if (W < 1) W = 1;
     while (W > 1 && (size_t)W * line_bytes > 110 * 1024) --W;
@@ -1002,7 +1174,7 @@ static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
     off = (off + 15) & ~(size_t)15;
     p.ioff = (int)off;
     p.LDH = 0;
-    p.smem = off + (size_t)W * nwl * 4 + (size_t)W * 4 + 16;
+    p.smem = off + (size_t)W * ints * 4 + 16;
     p.threads = W * p.G;
     p.tiles = make_tiles(g, 0, W);
     return p;
