@@ -69,13 +69,13 @@ def transpose_bytes_per_cell(launches_per_iter: float) -> float:
 # kernel source still matches the one the counters were taken on
 TRAFFIC = {
     # second sweeps (rows of a transposed field, no dot): launches 1 and 11 of the capture
-    "ct_pass_axis1": {"bytes": (67151616 + 11848960 + 67151616 + 11812608) / 2,
+    "ct_pass_axis1": {"bytes": (67174912 + 11857920 + 67174912 + 11739136) / 2,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "90773cf7f0042c05fb4e07e9d7f8d337ae800dc3a6b68393ca7037651b24c9cb"},
+                      "sha256": "1ba9de370ca1e6bb91b1ef6f27627d1090a6232aaa023d8d4d6c90f63c12f70e"},
     # first sweeps (with the dual dot on load): launches 9 and 12
-    "ct_pass_axis0": {"bytes": (134396416 + 26396416 + 136529920 + 27986688) / 2,
+    "ct_pass_axis0": {"bytes": (134357760 + 25629696 + 135288320 + 26567424) / 2,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "90773cf7f0042c05fb4e07e9d7f8d337ae800dc3a6b68393ca7037651b24c9cb"},
+                      "sha256": "1ba9de370ca1e6bb91b1ef6f27627d1090a6232aaa023d8d4d6c90f63c12f70e"},
 }
 
 
