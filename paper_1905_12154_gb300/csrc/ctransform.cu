@@ -194,6 +194,35 @@ __device__ __forceinline__ bool hidden_t(T a, T fa, T b, T fb, T c, T fc, T hh)
     return lhs >= rhs;
 }
 
+template <typename T>
+__device__ __forceinline__ T parab_t(T hh, T x, T j, T fj)
+{
+    const T d = x - j;
+    return fma(hh, d * d, fj);
+}
+
+// First grid cell owned by parabola b, the successor of a on the envelope
+// (FP32): the two meet at s = (f_b - f_a) / (2 hh (j_b - j_a)) + (j_a + j_b)/2
+// and b is the lower one right of s, so the cell is ceil(s), clamped to
+// [0, n].  For neighbours j_b - j_a < 16 apart an error of the rounded s
+// moves at most values within a fraction of an ulp; for wider gaps, where
+// the two parabolas separate faster, the cell is confirmed by comparing the
+// evaluated parabolas at it and at the cell before (the comparison the
+// sequential sweep makes), which the rounded s misses by at most one cell.
+__device__ __forceinline__ int start_cell(float ja, float fa, float jb, float fb, float hh, int n)
+{
+    const float d = jb - ja;
+    const float q = __fdividef(fb - fa, (2.f * hh) * d);
+    const float s = fmaf(0.5f, ja + jb, q);
+    int c = (int)fminf(fmaxf(ceilf(s), 0.f), (float)n);
+    if (d >= 16.f && c > 0) {
+        const float x = (float)c;
+        if (c < n && !(parab_t(hh, x, jb, fb) <= parab_t(hh, x, ja, fa))) ++c;
+        else if (parab_t(hh, x - 1.f, jb, fb) <= parab_t(hh, x - 1.f, ja, fa)) --c;
+    }
+    return c;
+}
+
 // Phase B as rounds of a parallel fix-up.  A parabola is on the envelope iff
 // its lifted point (j, f_j + hh j^2) is on the lower convex hull of the line's
 // points, and a point that lies on or above a chord between two other points
@@ -426,6 +455,74 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
             }
         }
         line_sync(w, G);
+        bool walk = sizeof(T) != 4;
+        if constexpr (sizeof(T) == 4) {
+            // ---- D (FP32): owners by marks, no sweep ---------------------------------
+            // The value array is free: each thread clears its cells to -1, then
+            // every envelope parabola k computes the first cell it owns from its
+            // predecessor (start_cell); a parabola owns cells iff the next one
+            // starts later, and then writes k at its start cell.  The owner of
+            // cell x is the last mark at or before x (marks grow with x).  A
+            // start that decreases (rounding between nearly collinear parabolas)
+            // sends the tile's lines to the sweep below.
+            int* mk = reinterpret_cast<int*>(f);
+            if (active)
+                for (int x = lo; x < hi; ++x) mk[SK::f(x)] = -1;
+            line_sync(w, G);
+            bool bad = false;
+            if (active && cnt > 0) {
+                const int H = htot[w];
+                const int k0 = incl - cnt;
+                float jc = (float)hidx[k0], fc = (float)hval[k0];
+                int cc = 0;
+                if (k0 > 0) cc = start_cell((float)hidx[k0 - 1], (float)hval[k0 - 1], jc, fc, (float)hh, n);
+                for (int k = k0; k < k0 + cnt; ++k) {
+                    int cn = n;
+                    float jn = 0.f, fn = 0.f;
+                    if (k + 1 < H) {
+                        jn = (float)hidx[k + 1]; fn = (float)hval[k + 1];
+                        cn = start_cell(jc, fc, jn, fn, (float)hh, n);
+                    }
+                    bad |= cn < cc;
+                    if (cn > cc) mk[SK::f(cc)] = k;
+                    jc = jn; fc = fn; cc = cn;
+                }
+            }
+            walk = group_or(bad, w, G);            // also publishes the marks
+            if (!walk) {
+                // the last mark in this thread's cells, then the last one before them
+                int last = -1;
+                if (active)
+                    for (int x = hi - 1; x >= lo && last < 0; --x) last = mk[SK::f(x)];
+                int inc = last;
+                for (int d = 1; d < width; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, d, width);
+                    if ((lane % width) >= d) inc = max(inc, y);
+                }
+                if (G > 32) {
+                    if ((t & 31) == 31) wsum_all[w * nwl + (t >> 5)] = inc;
+                    line_sync(w, G);
+                    for (int i = 0; i < (t >> 5); ++i) inc = max(inc, wsum_all[w * nwl + i]);
+                }
+                // exclusive: the last mark of the threads before this one
+                int prev = __shfl_up_sync(0xffffffffu, inc, 1, width);
+                if ((lane % width) == 0) prev = -1;
+                if (G > 32 && (lane % width) == 0)
+                    for (int i = 0; i < (t >> 5); ++i) prev = max(prev, wsum_all[w * nwl + i]);
+                if (active && lo < n) {
+                    int kc = prev;
+                    float jc = 0.f, fc = 0.f;
+                    if (kc >= 0) { jc = (float)hidx[kc]; fc = (float)hval[kc]; }
+                    for (int x = lo; x < hi; ++x) {
+                        const int m = mk[SK::f(x)];
+                        if (m >= 0) { kc = m; jc = (float)hidx[m]; fc = (float)hval[m]; }
+                        f[SK::f(x)] = (T)parab_t((float)hh, (float)x, jc, fc);
+                    }
+                }
+            }
+        }
+        if (walk) {
+        // ---- D: evaluate this thread's outputs by a sweep into the (now free) value array
         // ---- D: evaluate this thread's outputs into the (now free) value array -----
         if (active && lo < n) {
             const int H = htot[w];
@@ -454,6 +551,7 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
                 }
                 f[SK::f(x)] = vc;
             }
+        }
         }
         __syncthreads();
         // ---- store ---------------------------------------------------------------
@@ -523,12 +621,6 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T parab_t(T hh, T x, T j, T fj)
-{
-    const T d = x - j;
-    return fma(hh, d * d, fj);
-}
 
 // merge_pair with the cached end parabolas' indices held in T
 template <int K, typename T>
@@ -612,27 +704,6 @@ __device__ void merge_pair_t(const T* f, const short* stk, short* beg, short* en
 constexpr int kRowMinN = 256;          // rows longer than this take the row kernel
 constexpr int kRowLongN = 1024;        // from here 32 cells per thread, else 16
 
-// First grid cell owned by parabola b, the successor of a on the envelope
-// (FP32): the two meet at s = (f_b - f_a) / (2 hh (j_b - j_a)) + (j_a + j_b)/2
-// and b is the lower one right of s, so the cell is ceil(s), clamped to
-// [0, n].  For neighbours j_b - j_a < 16 apart an error of the rounded s
-// moves at most values within a fraction of an ulp; for wider gaps, where
-// the two parabolas separate faster, the cell is confirmed by comparing the
-// evaluated parabolas at it and at the cell before (the comparison the
-// sequential sweep makes), which the rounded s misses by at most one cell.
-__device__ __forceinline__ int start_cell(float ja, float fa, float jb, float fb, float hh, int n)
-{
-    const float d = jb - ja;
-    const float q = __fdividef(fb - fa, (2.f * hh) * d);
-    const float s = fmaf(0.5f, ja + jb, q);
-    int c = (int)fminf(fmaxf(ceilf(s), 0.f), (float)n);
-    if (d >= 16.f && c > 0) {
-        const float x = (float)c;
-        if (c < n && !(parab_t(hh, x, jb, fb) <= parab_t(hh, x, ja, fa))) ++c;
-        else if (parab_t(hh, x - 1.f, jb, fb) <= parab_t(hh, x - 1.f, ja, fa)) --c;
-    }
-    return c;
-}
 
 static int row_cells_per_thread(int n) { return n >= kRowLongN ? 32 : 16; }
 
@@ -882,7 +953,7 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
                 unsigned sword = 0u;
                 if (lo < n) {
                     sword = sw[lo >> 5];
-                    if (K < 32) sword = (sword >> (lo & 31)) & ((1u << K) - 1u);
+                    if (K < 32) sword = (sword >> (lo & 31)) & ((1u << (K & 31)) - 1u);
                 }
                 const int v = (nb << 16) | __popc(sword);
                 int incl = v;
