@@ -216,6 +216,17 @@ def random_field(shape, seed, scale=1.0):
     return scale * np.random.default_rng(seed).standard_normal(shape)
 
 
+def quadratic_potential(shape_xyz, seed):
+    """phi(x) = |x|^2/2 - a.x with a seeded a in [0.2, 0.8]^d: along every grid
+    line |x|^2/2 - phi is affine, so all the line's lifted points lie on one
+    line (up to the rounding of phi) -- the degenerate case of the lower
+    envelope, where many parabolas meet at nearly one point."""
+    rng = np.random.default_rng(seed)
+    xs = centres(shape_xyz)
+    a = rng.uniform(0.2, 0.8, size=len(shape_xyz))
+    return sum(0.5 * xs[k] ** 2 - a[k] * xs[k] for k in range(len(shape_xyz)))
+
+
 def smooth_potential(shape_xyz, seed, amp=0.05):
     """A smooth random potential (sum of a few cosines) of small amplitude,
     the kind of field the method's iterates are."""

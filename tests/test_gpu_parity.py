@@ -69,6 +69,26 @@ def test_ctransform_fp32(B, shape):
     assert np.max(np.abs(got - want)) <= 4 * np.finfo(np.float32).eps * scale
 
 
+# |x|^2/2 - phi affine along every line: the rounded FP32 values leave many
+# parabolas on the envelope that meet at nearly one point, where the FP32
+# owner ranking can see start cells decrease and hands the line to the sweep;
+# rows of 4096 and 1500 (row kernel), 300-cell columns and short rows (tiles)
+DEGENERATE_SHAPES = [(4096, 3), (6, 1500), (300, 64), (40, 200), (5, 384, 9)]
+
+
+@pytest.mark.parametrize("shape", DEGENERATE_SHAPES, ids=str)
+def test_ctransform_degenerate_envelope(B, shape):
+    phi = si.quadratic_potential(tuple(reversed(shape)), 7)
+    scale = 1.0 + np.max(np.abs(phi))
+    want = oracle.ctransform(phi, "linear")
+    got = host(B.bfm_ctransform(dev(phi)))
+    assert np.max(np.abs(got - want)) <= 1e-12 * scale
+    phi32 = phi.astype(np.float32)
+    want32 = oracle.ctransform(phi32.astype(np.float64), "linear")
+    got32 = host(B.bfm_ctransform(dev(phi32, torch.float32)))
+    assert np.max(np.abs(got32 - want32)) <= 4 * np.finfo(np.float32).eps * scale
+
+
 def test_ctransform_in_place_and_invariants(B):
     phi = dev(si.random_field((40, 56), 4, 0.1))
     c1 = B.bfm_ctransform(phi)
