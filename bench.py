@@ -252,7 +252,8 @@ def paper_comparison(B, dev, stream) -> dict:
 
 
 def other_workloads(B, dev, stream, args) -> dict:
-    """The 384^3 3D solve, 128 batched uneven problems and the 32-pair loss."""
+    """The 384^3 3D solve, 128 batched uneven problems, the 32-pair loss, a
+    separable power-cost solve and displacement interpolation."""
     import numpy as np
     import torch
     import synthetic_inputs as si
@@ -310,6 +311,37 @@ def other_workloads(B, dev, stream, args) -> dict:
     _, tbk = timed(lambda: torch.autograd.grad(loss.sum(), [mu, nu]))
     out["loss_32x256_fp32"] = {"pairs": 32, "forward_s": tf, "backward_s": tbk,
                                "pairs_per_s": 32 / (tf + tbk)}
+    del mu, nu, loss
+    # separable power cost (Section 5): the diagonal discs to the anti-diagonal
+    # ones with p = (1.1, 3), 1024^2, FP32; time per iteration from two solve
+    # lengths (set-up cancels), cost against the closed form (1/2)^3/3 = 1/24
+    p = (1.1, 3.0)
+    dmu, dnu = si.diagonal_to_antidiagonal_discs(1024)
+    pm = torch.from_numpy(dmu).to(dev, torch.float32)
+    pn = torch.from_numpy(dnu).to(dev, torch.float32)
+    B.bfm_solve(pm, pn, tol=0.0, max_iter=2, p=p, with_map=False)
+    _, t10 = timed(lambda: B.bfm_solve(pm, pn, tol=0.0, max_iter=10, p=p, with_map=False))
+    r30, t30 = timed(lambda: B.bfm_solve(pm, pn, tol=0.0, max_iter=30, p=p, with_map=False))
+    ms = (t30 - t10) / 20 * 1e3
+    out["power_cost_1024_fp32"] = {"p": list(p), "ms_per_iter": ms, "iters_per_s": 1e3 / ms,
+                                   "cost": float(r30["dual"][-1]), "exact_cost": 1.0 / 24.0,
+                                   "abs_error": abs(float(r30["dual"][-1]) - 1.0 / 24.0)}
+    del pm, pn
+    # displacement interpolation (Section 4.3): rho_t = ((1 - t) x + t T) # mu at
+    # t = 1/2 with the map of the translated discs, 2048^2, FP32; 20 B per cell
+    # at most (read the map's two components and mu, zero and write rho)
+    tmu, tnu = si.translated_discs(2048)
+    im = torch.from_numpy(tmu).to(dev, torch.float32)
+    inu = torch.from_numpy(tnu).to(dev, torch.float32)
+    rr = B.bfm_solve(im, inu, tol=0.0, max_iter=6, with_map=True)
+    rho = torch.empty_like(im)
+    B.bfm_interpolate(rr["map"], im, 0.5, out=rho)
+    _, ti = timed(lambda: [B.bfm_interpolate(rr["map"], im, 0.5, out=rho) for _ in range(20)])
+    ms = ti / 20 * 1e3
+    cells = im.numel()
+    out["interpolation_2048_fp32"] = {"t": 0.5, "ms_per_call": ms,
+                                      "gbs_at_20_bytes_per_cell": 20 * cells / (ms * 1e-3) / 1e9,
+                                      "mass": float(rho.double().mean().item())}
     return out
 
 
@@ -325,7 +357,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-budget-s", type=float, default=150.0)
     ap.add_argument("--no-workloads", action="store_true",
-                    help="skip the 3D, batched and loss workloads")
+                    help="skip the 3D, batched, loss, power-cost and interpolation workloads")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
