@@ -382,17 +382,29 @@ def bfm_solve(mu, nu, tol: float = 1e-6, max_iter: int = 300, with_map: bool = T
 
 
 def bfm_solve_host(mu: np.ndarray, nu: np.ndarray, tol: float = 1e-6, max_iter: int = 300,
-                   with_map: bool = True, workspace=None, device=None, **opts) -> dict:
+                   with_map: bool = True, workspace=None, device=None, out=None, **opts) -> dict:
     """bfm_solve on host (numpy) arrays: the library copies the inputs to the
-    device workspace and the results back."""
+    device workspace and the results back.  out: optional dict of C-contiguous
+    arrays "phi", "psi" (and "map" with with_map) of the inputs' dtype that
+    receive the results, e.g. views of page-locked memory, which copies
+    faster than freshly allocated pageable arrays."""
     import torch
     dt = np.float32 if mu.dtype == np.float32 else np.float64
     prec = BFM_FP32 if dt == np.float32 else BFM_FP64
     mu = np.ascontiguousarray(mu, dtype=dt); nu = np.ascontiguousarray(nu, dtype=dt)
     g = grid_of(mu.shape)
     nd = mu.ndim
-    phi = np.empty_like(mu); psi = np.empty_like(mu)
-    tmap = np.empty((nd,) + mu.shape, dtype=dt) if with_map else None
+
+    def given(name, shape):
+        a = (out or {}).get(name)
+        if a is None:
+            return np.empty(shape, dtype=dt)
+        if a.shape != shape or a.dtype != dt or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
+            raise ValueError(f"out[{name!r}] must be a writeable C-contiguous {np.dtype(dt).name} "
+                             f"array of shape {shape}")
+        return a
+    phi = given("phi", mu.shape); psi = given("psi", mu.shape)
+    tmap = given("map", (nd,) + mu.shape) if with_map else None
     L = max_iter + 1
     dual = np.zeros(L); resid = np.zeros(L); sig = np.zeros(L)
     res = bfm_result()

@@ -286,6 +286,15 @@ def test_solve_host_buffers(B):
     ref = oracle.solve(mu, nu, tol=0.0, max_iter=5)
     assert abs(r["w2sq"] - ref["w2sq"]) < 1e-12
     assert np.max(np.abs(r["phi"] - ref["phi"])) < 1e-10
+    # results into caller-owned page-locked arrays: the same values, in place
+    outs = {k: torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
+            for k, shape in (("phi", mu.shape), ("psi", mu.shape), ("map", (2,) + mu.shape))}
+    r2 = B.bfm_solve_host(mu, nu, tol=0.0, max_iter=5, out=outs)
+    assert r2["phi"] is outs["phi"] and r2["map"] is outs["map"]
+    for k in ("phi", "psi", "map"):
+        assert np.array_equal(r2[k], r[k])
+    with pytest.raises(ValueError):
+        B.bfm_solve_host(mu, nu, tol=0.0, max_iter=5, out={"phi": np.empty((3, 3))})
 
 
 def test_solve_converges_and_stops(B):
