@@ -1,0 +1,84 @@
+"""Parity at the benchmark's full size (marked gpu).
+
+The 4096 x 4096 annulus -> 5 Gaussians workload in FP32 runs through the
+step-wise solver, i.e. the launch configuration the benchmark times (row
+sweeps of the c-transform, transposed copies for the long columns, psi kept
+transposed between half steps, the compile-time DCT row passes, the vector
+pushforward).  The oracle cannot run the whole solve at this size within a
+test, so the checks are the ones it can make exactly:
+  * psi = phi^c (Definition 2.1) at sampled cells, each the minimum over all
+    16.7 M grid points computed in FP64 from the FP32 phi: 4 ulp of the field
+    scale, the tolerance of the smaller FP32 c-transform tests;
+  * the map of every cell against the oracle's map of the same psi (central
+    differences, clamped to the box of cell centres): FP32 rounding of a cell
+    position is below 2.5e-4 cells, so 1e-5 of the unit box;
+  * the pushforward of mu by that map conserves mass (Lemma 3.1).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+N = 4096
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1905_12154_gb300 import binding
+    binding.lib()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def solved(B):
+    mu, nu = si.workload_annulus_5g_4096(N)
+    m = torch.as_tensor(mu, dtype=torch.float32, device="cuda")
+    n = torch.as_tensor(nu, dtype=torch.float32, device="cuda")
+    s = B.BfmSolver(m, n, tol=0.0, max_iter=10)
+    s.iterate(2)
+    r = s.finish(with_map=True)
+    torch.cuda.synchronize()
+    return dict(mu=mu, mu32=m, phi=r["phi"].double().cpu().numpy(),
+                psi=r["psi"].double().cpu().numpy(), psi_dev=r["psi"],
+                map=r["map"].double().cpu().numpy(), iters=r["iters"], dual=r["dual"])
+
+
+def test_full_size_solver_runs(solved):
+    assert solved["iters"] == 2
+    assert np.all(np.isfinite(solved["dual"]))
+    assert np.all(np.isfinite(solved["phi"])) and np.all(np.isfinite(solved["psi"]))
+
+
+def test_full_size_psi_is_phi_c_at_sampled_cells(solved):
+    phi, psi = solved["phi"], solved["psi"]
+    hh = 0.5 / (N * N)
+    idx = np.arange(N, dtype=np.float64)
+    rng = np.random.default_rng(4096)
+    cells = [(0, 0), (N - 1, N - 1), (0, N - 1), (N - 1, 0)]
+    cells += [tuple(int(v) for v in rng.integers(0, N, size=2)) for _ in range(28)]
+    scale = 1.0 + np.max(np.abs(phi))
+    for (i, j) in cells:                       # i along axis 0 (x), j along axis 1 (y)
+        row_cost = hh * (i - idx) ** 2         # over i'
+        col_cost = hh * (j - idx) ** 2         # over j'
+        inner = np.min(row_cost[None, :] - phi, axis=1)          # for each j'
+        want = np.min(col_cost + inner)
+        got = psi[j, i]
+        assert abs(got - want) <= 4 * np.finfo(np.float32).eps * scale, (i, j, got, want)
+
+
+def test_full_size_map_against_oracle(solved):
+    want = oracle.transport_map(solved["psi"])
+    assert np.max(np.abs(solved["map"] - want)) <= 1e-5
+
+
+def test_full_size_pushforward_mass(B, solved):
+    rho = B.bfm_pushforward(solved["psi_dev"], solved["mu32"])
+    torch.cuda.synchronize()
+    total = rho.double().sum().item()
+    want = solved["mu32"].double().sum().item()
+    assert abs(total - want) <= 1e-5 * want
