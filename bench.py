@@ -64,8 +64,8 @@ def transpose_bytes_per_cell(launches_per_iter: float) -> float:
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# of the launches of that kind in one cold-cache ncu capture, summarised in
-# profiles/ct_row_kernel_annulus5g_4096_fp32.md); reported only while the
+# of the launches of that kind in one cold-cache ncu capture of the 4096^2
+# solve, whose summary sits under profiles/); reported only while the
 # kernel source still matches the one the counters were taken on
 TRAFFIC = {
     # second sweeps (rows of a transposed field, no dot): launches 1 and 11 of the capture

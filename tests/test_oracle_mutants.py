@@ -38,6 +38,14 @@ MUTANTS = [
     ("bilinear_swap", "w *= up ? w1[a] : (1.0 - w1[a]);", "w *= up ? (1.0 - w1[a]) : w1[a];", 0),
     ("deposit_floor", "int i = (int)floor(pos);", "int i = (int)floor(pos + 0.5);", 0),
     ("step_rule_inverted", "if (gain < o->beta1 * sigma * G) {", "if (gain > o->beta1 * sigma * G) {", 0),
+    ("step_rule_alpha_swapped_decrease", "double s = o->alpha2 * sigma;", "double s = o->alpha1 * sigma;", 0),
+    ("step_rule_alpha_swapped_increase", "return o->alpha1 * sigma;", "return o->alpha2 * sigma;", 0),
+    ("step_rule_window_collapsed", "if (gain > o->beta2 * sigma * G)", "if (gain > o->beta1 * sigma * G)", 0),
+    ("step_rule_beta2_doubled", "if (gain > o->beta2 * sigma * G)", "if (gain > 2.0 * o->beta2 * sigma * G)", 0),
+    ("step_rule_floor_dropped", "return (s > floor_) ? s : floor_;", "return s;", 0),
+    ("step_rule_no_growth", "if (gain > o->beta2 * sigma * G) return o->alpha1 * sigma;", "", 0),
+    ("residual_uniform_fallback_dropped", "double r = (Gref > 0) ? sqrt(fmax(G, 0.0) / Gref) : sqrt(fmax(G, 0.0));",
+     "double r = sqrt(fmax(G, 0.0) / Gref);", None),
     ("sigma0_constant", "8.0 * fmin(1.0 / mx_mu, 1.0 / mx_nu)", "4.0 * fmin(1.0 / mx_mu, 1.0 / mx_nu)", 0),
     ("w2_factor", "info_out[2] = 2.0 * Jold;", "info_out[2] = Jold;", 0),
     ("psi_half_measure", "bfm_oracle_pushforward_p(tmp, nu, rho, ndim, n, pc);",
@@ -55,6 +63,8 @@ MUTANTS = [
 
 
 def _replace_nth(text, old, new, k):
+    if k is None:
+        return text.replace(old, new)
     pos = -1
     for _ in range(k + 1):
         pos = text.index(old, pos + 1)

@@ -380,6 +380,78 @@ def pin_step_rule_constants():
     assert abs(r["sigma"][0] - 8.0 / max(mu.max(), nu.max())) < 1e-15
 
 
+def _first_steps(**opts):
+    mu, nu = si.translated_discs(32)
+    s0 = 8.0 / max(mu.max(), nu.max())
+    return s0, oracle.solve(mu, nu, tol=0.0, max_iter=6, **{k: (v * s0 if k == "sigma0" else v)
+                                                             for k, v in opts.items()})
+
+
+def pin_step_rule_shrinks_on_overshoot():
+    """Section 4.2: a step far too long loses dual value (the gain is below
+    beta1 sigma G), so every half step multiplies sigma by alpha2 = 4/5: 0.64
+    per iteration until the step fits."""
+    _, r = _first_steps(sigma0=1000.0)
+    ratio = r["sigma"][1:] / r["sigma"][:-1]
+    assert np.all(np.abs(ratio - 0.64) < 1e-14), ratio
+
+
+def pin_step_rule_grows_on_short_step():
+    """Section 4.2: for a short step the dual value rises by about sigma G
+    (first order in sigma, Lemma 2.3's gradient), above beta2 sigma G = 3/4
+    sigma G, so every half step multiplies sigma by alpha1 = 5/4: 25/16 per
+    iteration."""
+    _, r = _first_steps(sigma0=1e-3)
+    ratio = r["sigma"][1:] / r["sigma"][:-1]
+    assert np.all(np.abs(ratio - 1.5625) < 1e-14), ratio
+
+
+def pin_step_rule_floor():
+    """Section 4.2: decreases never take sigma below sigma_min.  With
+    sigma_min set far above the stable step, sigma falls by 0.64 per
+    iteration from 50 and then stays at sigma_min exactly."""
+    mu, nu = si.translated_discs(32)
+    r = oracle.solve(mu, nu, tol=0.0, max_iter=14, sigma0=50.0, sigma_min=1.0)
+    s = r["sigma"]
+    assert s.min() == 1.0 and np.all(s[-4:] == 1.0), s
+    k = int(np.argmax(s == 1.0))
+    assert np.all(np.abs(s[1:k] / s[:k - 1] - 0.64) < 1e-14), s
+
+
+def pin_step_rule_window():
+    """Section 4.2: a gain between beta1 sigma G and beta2 sigma G keeps sigma.
+    On the paper's two discs from the paper's sigma_0 some iteration changes
+    sigma by exactly one factor alpha2 (one half step shrinks, the other is
+    kept), and once sigma has settled it is kept for whole iterations."""
+    mu, nu = si.translated_discs(32)
+    r = oracle.solve(mu, nu, tol=0.0, max_iter=30)
+    ratio = r["sigma"][1:] / r["sigma"][:-1]
+    assert np.any(np.abs(ratio - 0.8) < 1e-14), ratio
+    assert np.all(ratio[-10:] == 1.0), ratio
+
+
+def pin_residual_uniform_target():
+    """A uniform target has ||nu - 1||_{H^-1} = 0, so the residual is the
+    absolute H^-1 norm of nu - T#mu there (reading of the stopping norm).  At
+    phi_0 = 0 the map is the identity and T#mu = mu, so r_0 = ||1 -
+    mu||_{H^-1} = sqrt(hd sum_k c_k^2 / lambda_k) with c the orthonormal
+    DCT-II of 1 - mu (scipy) and lambda_k the Neumann eigenvalues."""
+    rng = np.random.default_rng(3)
+    mu = si.normalise(si.gaussian_mixture((24, 20), rng.uniform(0.3, 0.7, (2, 2)), [0.12, 0.1]))
+    nu = np.ones_like(mu)
+    r = oracle.solve(mu, nu, tol=0.0, max_iter=4)
+    f = 1.0 - mu
+    c = scipy.fft.dctn(f, type=2, norm="ortho")
+    n1, n0 = f.shape
+    k1 = np.arange(n1)[:, None]
+    k0 = np.arange(n0)[None, :]
+    lam = 4 * n0**2 * np.sin(np.pi * k0 / (2 * n0))**2 + 4 * n1**2 * np.sin(np.pi * k1 / (2 * n1))**2
+    lam[0, 0] = np.inf
+    want = np.sqrt(np.sum(c**2 / lam) / f.size)
+    assert abs(r["resid"][0] - want) < 1e-13 * want
+    assert np.all(np.isfinite(r["resid"])) and r["resid"][-1] < 0.5 * r["resid"][0]
+
+
 FAST_PINS = [
     pin_ct_splitting_equals_definition, pin_ct_linear_matches_brute,
     pin_ct_lemma22_properties, pin_ct_closed_forms, pin_dct_matches_scipy,
@@ -387,6 +459,8 @@ FAST_PINS = [
     pin_pushforward_identity_and_mass, pin_pushforward_translation,
     pin_map_quadratic_and_bilinear_weights, pin_solve_translated_discs,
     pin_solve_chain_invariants, pin_step_rule_constants, pin_interpolate_translation,
+    pin_step_rule_shrinks_on_overshoot, pin_step_rule_grows_on_short_step,
+    pin_step_rule_floor, pin_step_rule_window, pin_residual_uniform_target,
 ]
 ALL_PINS = FAST_PINS + [pin_solve_square_to_four, pin_gradient_ascent_baseline,
                         pin_power_cost_definition_and_p2, pin_power_cost_translation,
