@@ -181,7 +181,8 @@ __device__ __forceinline__ bool group_or(bool v, int w, int G)
     return r != 0;
 }
 
-constexpr int kFixRounds = 6;          // boundary fix-up rounds before the merges take over
+constexpr int kFixRounds = 6;          // tile lines: fix-up rounds before the merges take over
+constexpr int kFixRoundsRow = 16;      // row groups: the same
 
 // Parabola indices held in T: differences of indices below 2^24 are exact in
 // FP32, so these give the same values as the integer forms above while
@@ -229,16 +230,70 @@ __device__ __forceinline__ int start_cell(float ja, float fa, float jb, float fb
 // of the line (one on each side) is not.  Each chunk stack is a convex chain,
 // so in their concatenation only the stacks' ends can be reflex: in a round
 // every thread reads the ends of the neighbouring non-empty stacks, then drops
-// its own first entries while they lie above the chord from the left
-// neighbour's last entry, and its last entries while they lie above the chord
-// to the right neighbour's first.  Returns whether any thread of the line
-// group dropped anything (the rounds end when none did: the stacks then form
-// the hull).
+// its own first entries while they lie on or above the chord from the left
+// neighbour's last entry a to the entry after them, and its last entries
+// while they lie on or above the chord from the entry before them to the
+// right neighbour's first entry c.  The rounds end when no thread of the line
+// dropped anything: the stacks then form the hull.
+//
+// Along a convex chain b_0, b_1, ... the slope from a to b_{k+1} is a
+// weighted mean of the slope from a to b_k and the chain's slope from b_k to
+// b_{k+1}; so the first test ("b_k on or above the chord a b_{k+1}", i.e. the
+// slope a->b_k is at least the chain's slope at b_k) holds for a prefix of
+// the chain and fails from the first k where it fails (the tangent from a).
+// Mirrored, the second test holds for a suffix.  Each boundary is therefore
+// found by one direct test and, only when that one drops, a binary search:
+// at most 1 + log2(K) tests instead of up to K dependent ones.  The test of
+// the stack's last entry against c (after all others dropped) is not part of
+// the chain and is made last, as the sequential scan makes it.
+template <int K, typename T>
+__device__ __forceinline__ void drop_ends(const T* f, const short* stk, int& b0, int& e1,
+                                          int pa, int pc, T hh)
+{
+    using SK = Skew<K>;
+    auto J = [&](int p) { return (T)stk[SK::s(p)]; };
+    auto V = [&](int p) { return f[SK::f(p)]; };
+    T jc = (T)0, fc = (T)0;
+    if (pc >= 0) { jc = J(pc); fc = V(pc); }
+    if (pa >= 0) {
+        const T ja = J(pa), fa = V(pa);
+        // entry p (p + 1 < e1) on or above the chord from a to entry p + 1
+        auto front = [&](int p) { return hidden_t(ja, fa, J(p), V(p), J(p + 1), V(p + 1), hh); };
+        int p = b0;
+        if (e1 - b0 >= 2 && front(b0)) {
+            int lo = b0 + 1, hi = e1 - 1;          // first failing test in [b0 + 1, e1 - 2], else e1 - 1
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (front(mid)) lo = mid + 1;
+                else hi = mid;
+            }
+            p = lo;
+        }
+        if (p == e1 - 1 && pc >= 0 && hidden_t(ja, fa, J(p), V(p), jc, fc, hh)) p = e1;
+        b0 = p;
+    }
+    if (pc >= 0 && e1 - 1 > b0) {
+        // entry p (p > b0) on or above the chord from entry p - 1 to c
+        auto back = [&](int p) { return hidden_t(J(p - 1), V(p - 1), J(p), V(p), jc, fc, hh); };
+        if (back(e1 - 1)) {
+            int lo = b0 + 1, hi = e1 - 1;          // first holding test in [b0 + 1, e1 - 1]
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (back(mid)) hi = mid;
+                else lo = mid + 1;
+            }
+            e1 = lo;
+        }
+    }
+}
+
+// One round for lines of a tile (G threads per line, possibly several lines
+// per warp); the neighbouring non-empty stacks are found by scanning.
+// Returns whether any thread of the line group dropped anything.
 template <int K, typename T>
 __device__ __forceinline__ bool fix_round(const T* f, const short* stk, short* beg, short* end,
                                           int t, int G, int w, T hh, bool active)
 {
-    using SK = Skew<K>;
     int b0 = 0, e1 = 0, pa = -1, pc = -1;          // own range, neighbours' end entries
     if (active) {
         b0 = beg[t];
@@ -256,28 +311,9 @@ __device__ __forceinline__ bool fix_round(const T* f, const short* stk, short* b
     else asm volatile("bar.sync %0, %1;" :: "r"(1 + w), "r"(G) : "memory");
     bool dropped = false;
     if (e1 > b0) {
-        T ja = (T)0, fa = (T)0, jc = (T)0, fc = (T)0;
-        if (pa >= 0) { ja = (T)stk[SK::s(pa)]; fa = f[SK::f(pa)]; }
-        if (pc >= 0) { jc = (T)stk[SK::s(pc)]; fc = f[SK::f(pc)]; }
-        if (pa >= 0) {
-            while (b0 < e1) {
-                T jr, fr;
-                if (b0 + 1 < e1) { jr = (T)stk[SK::s(b0 + 1)]; fr = f[SK::f(b0 + 1)]; }
-                else if (pc >= 0) { jr = jc; fr = fc; }
-                else break;
-                if (!hidden_t(ja, fa, (T)stk[SK::s(b0)], f[SK::f(b0)], jr, fr, hh)) break;
-                ++b0;
-                dropped = true;
-            }
-        }
-        if (pc >= 0) {
-            while (e1 - 1 > b0 &&
-                   hidden_t((T)stk[SK::s(e1 - 2)], f[SK::f(e1 - 2)], (T)stk[SK::s(e1 - 1)],
-                            f[SK::f(e1 - 1)], jc, fc, hh)) {
-                --e1;
-                dropped = true;
-            }
-        }
+        const int ob = b0, oe = e1;
+        drop_ends<K>(f, stk, b0, e1, pa, pc, hh);
+        dropped = (b0 != ob) || (e1 != oe);
         if (dropped) { beg[t] = (short)b0; end[t] = (short)e1; }
     }
     return group_or(dropped, w, G);                // also publishes the updates
@@ -715,6 +751,39 @@ __device__ __forceinline__ void group_sync(int w, int G)
     else asm volatile("bar.sync %0, %1;" :: "r"(1 + w), "r"(G) : "memory");
 }
 
+// One round for a row group (G >= 32 threads, whole warps).  The nearest
+// non-empty stacks come from the row's mask of non-empty chunks (one bit per
+// thread, nem[G / 32]), so runs of emptied chunks cost a few word reads
+// instead of a walk; each round's ballot refreshes the mask.
+template <int K, typename T>
+__device__ __forceinline__ bool fix_round_row(const T* f, const short* stk, short* beg, short* end,
+                                              unsigned* nem, int t, int G, int w, T hh)
+{
+    const int nwl = G >> 5;
+    int b0 = beg[t], e1 = end[t], pa = -1, pc = -1;
+    if (e1 > b0) {
+        int wi = t >> 5;
+        unsigned m = nem[wi] & ((1u << (t & 31)) - 1u);
+        while (m == 0u && wi > 0) m = nem[--wi];
+        if (m) pa = end[(wi << 5) + 31 - __clz(m)] - 1;
+        wi = t >> 5;
+        m = nem[wi] & (0xfffffffeu << (t & 31));
+        while (m == 0u && wi + 1 < nwl) m = nem[++wi];
+        if (m) pc = beg[(wi << 5) + __ffs(m) - 1];
+    }
+    group_sync(w, G);                              // every read before any update
+    bool dropped = false;
+    if (e1 > b0) {
+        const int ob = b0, oe = e1;
+        drop_ends<K>(f, stk, b0, e1, pa, pc, hh);
+        dropped = (b0 != ob) || (e1 != oe);
+        if (dropped) { beg[t] = (short)b0; end[t] = (short)e1; }
+    }
+    const unsigned ne = __ballot_sync(0xffffffffu, e1 > b0);
+    if ((t & 31) == 0) nem[t >> 5] = ne;
+    return group_or(dropped, w, G);                // also publishes the updates and the mask
+}
+
 // BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
 template <typename T, int K, bool BATCHED>
 __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtArgs<T>* batch)
@@ -749,6 +818,7 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
     short* end = beg + G;
     short* nzs = end + G;
     int* wsum = wsum_all + w * 2 * nwl;
+    unsigned* nem = reinterpret_cast<unsigned*>(wsum);   // phase B: mask of non-empty chunks
     int* cnt = cnt_all + 2 * w;
     unsigned* sw = sw_all + (size_t)w * nsw;
     unsigned* wbm = wbm_all + (size_t)w * G;
@@ -843,13 +913,17 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
             beg[t] = 0;
             end[t] = 0;
         }
+        {
+            const unsigned ne = __ballot_sync(0xffffffffu, lo < n);
+            if (lane == 0) nem[t >> 5] = ne;
+        }
         group_sync(w, G);
         // ---- B: envelope of the whole line ------------------------------------
-        // Rounds that drop reflex stack ends (see fix_round), then pairwise
-        // merges for lines still changing after kFixRounds rounds.
+        // Rounds that drop reflex stack ends (see fix_round_row), then
+        // pairwise merges for rows still changing after kFixRoundsRow rounds.
         bool moved = true;
-        for (int round = 0; round < kFixRounds && moved; ++round)
-            moved = fix_round<K>(f, stk, beg, end, t, G, w, hh, true);
+        for (int round = 0; round < kFixRoundsRow && moved; ++round)
+            moved = fix_round_row<K>(f, stk, beg, end, nem, t, G, w, hh);
         if (moved) {
             for (int s = 1; s < G; s <<= 1) {
                 if ((t & (2 * s - 1)) == 0 && t + s < G) merge_pair_t<K>(f, stk, beg, end, t, s, n, hh);

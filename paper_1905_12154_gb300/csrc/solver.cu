@@ -20,6 +20,8 @@
 #include <string.h>
 #include <math.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "state.cuh"
@@ -239,10 +241,21 @@ struct Profiler {
 };
 static thread_local Profiler g_prof;
 
+// Each kernel group also opens an NVTX range named like its profiler kind (a
+// no-op unless a tool is attached; inside a stream capture the range marks
+// the enqueue, not the replay).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct ProfScope {
     ProfRec* r = nullptr;
     cudaStream_t st;
-    ProfScope(int kind, int launches, cudaStream_t s) : st(s)
+    NvtxRange nv;
+    ProfScope(int kind, int launches, cudaStream_t s) : st(s), nv(kProfNames[kind])
     {
         if (!g_prof.on) return;
         if (g_prof.used >= g_prof.cap) { g_prof.dropped++; return; }
@@ -478,6 +491,7 @@ template <typename T>
 bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
                             Logs logs, cudaStream_t st, const double* pc)
 {
+    NvtxRange nv(phi_half ? "bfm_phi_half_step" : "bfm_psi_half_step");
     const double hd = 1.0 / (double)g.N;
     const int* done = &w->state->done;
     T* mu = (T*)w->mu_n;
@@ -1004,6 +1018,7 @@ extern "C" bfm_status bfm_solve(const void* mu, const void* nu, const bfm_grid* 
                                 bfm_result* out)
 {
     if (!out) return BFM_ERR_INVALID_ARG;
+    NvtxRange nv("bfm_solve");
     bfm_status s = bfm_solver_init(mu, nu, grid, cost, prec, tol, max_iter, opt, workspace,
                                    workspace_bytes, stream, out->phi, out->psi);
     if (s != BFM_OK) return s;

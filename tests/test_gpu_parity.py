@@ -321,6 +321,25 @@ def test_solve_rejects_bad_input(B):
     assert e.value.status == B.BFM_ERR_WORKSPACE
 
 
+def test_solve_nonfinite_returns_status(B):
+    """A non-finite dual value or gradient norm ends the solve with
+    BFM_ERR_NONFINITE (made on the host: nothing faults).  FP32: a first step
+    of 1e300 turns phi into infinities; FP64: a warm start whose phi is
+    infinite on the target's support.  The context stays usable."""
+    mu, nu = si.translated_discs(32)
+    with pytest.raises(B.BfmError) as e:
+        B.bfm_solve(dev(mu, torch.float32), dev(nu, torch.float32), tol=0.0, max_iter=4,
+                    sigma0=1e300)
+    assert e.value.status == B.BFM_ERR_NONFINITE
+    phi0 = np.where(nu > 0, np.inf, 0.0)
+    with pytest.raises(B.BfmError) as e:
+        B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=4, phi_init=dev(phi0))
+    assert e.value.status == B.BFM_ERR_NONFINITE
+    r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=2)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=2)
+    assert abs(r["w2sq"] - ref["w2sq"]) < 1e-12
+
+
 def test_solve_max_iter_zero(B):
     mu, nu = si.translated_discs(16)
     r = B.bfm_solve(dev(mu), dev(nu), tol=0.0, max_iter=0)
