@@ -83,3 +83,24 @@ def test_algorithmic_bytes_per_iteration():
     assert abs(b.transpose_bytes_per_cell(10) - (2 * 12 + 8 * 8) / 10) < 1e-12
     assert b.transpose_bytes_per_cell(8) == 8
     assert b.BYTES_PER_CELL_2D_TRANSPOSED["ct_pass_axis1"] == 8
+
+
+def test_map_difference_separates_split_points():
+    """A map that jumps by 10 cells along one column (mass split between two
+    targets): an FP32 map that sends the cells beside the jump to the other
+    side differs by 10 cells there, but by 0.01 cells off the split points."""
+    import torch
+    b = _bench()
+    n = 16
+    x = (torch.arange(n, dtype=torch.float64) + 0.5) / n
+    X, Y = x[None, :].expand(n, n), x[:, None].expand(n, n)
+    m64 = torch.stack([X.clone(), Y.clone()])
+    m64[0, :, 8:] += 10.0 / n                     # the jump between columns 7 and 8
+    m32 = m64.clone()
+    m32[0] += 0.01 / n
+    m32[0, :, 8] -= 10.0 / n                      # column 8 lands on the other side
+    mu = torch.ones(n, n, dtype=torch.float64)
+    r = b.map_difference(m32, m64, mu, n)
+    assert abs(r["map_linf_cells_on_mu_support"] - 9.99) < 1e-9
+    assert abs(r["map_linf_cells_off_split_points"] - 0.01) < 1e-9
+    assert abs(r["split_points_mass_share"] - 4.0 / n) < 1e-12   # columns 6-9

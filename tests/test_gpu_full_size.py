@@ -12,7 +12,22 @@ test, so the checks are the ones it can make exactly:
   * the map of every cell against the oracle's map of the same psi (central
     differences, clamped to the box of cell centres): FP32 rounding of a cell
     position is below 2.5e-4 cells, so 1e-5 of the unit box;
-  * the pushforward of mu by that map conserves mass (Lemma 3.1).
+  * the pushforward of mu by that map conserves mass (Lemma 3.1);
+and, after 10 iterations, the parts of the next phi-half step cell by cell
+on the whole grid, each against the oracle applied to the GPU's own input
+to that part (widened to FP64), so that each tolerance is the FP32 rounding
+of that part alone:
+  * psi~ = phi_10^c against the oracle's Legendre-line transform of phi_10
+    (Section 4.1): 4 ulp of the field scale;
+  * rho = T#mu from the GPU's psi~ against the oracle's pushforward of the
+    same psi~ (Lemma 3.1): positions carry FP32 rounding of n^2 (psi_{i+1} -
+    psi_{i-1}) / 4, below 1e-4 cells for displacements of a few hundred
+    cells, so each bilinear weight moves by less than that and rho by less
+    than 2e-5 of its maximum;
+  * g = (-Delta)^{-1}(nu - rho) (Lemma 2.3) from the GPU's f = nu - rho
+    against the oracle's FFT Poisson solve of the same f: FP32 rounding over
+    the 12 + 12 radix stages of two 4096-point FFT passes, 2e-5 of max |g|,
+    and G to the same relative tolerance.
 """
 import numpy as np
 import pytest
@@ -82,3 +97,47 @@ def test_full_size_pushforward_mass(B, solved):
     total = rho.double().sum().item()
     want = solved["mu32"].double().sum().item()
     assert abs(total - want) <= 1e-5 * want
+
+
+@pytest.fixture(scope="module")
+def ten(B):
+    mu, nu = si.workload_annulus_5g_4096(N)
+    m = torch.as_tensor(mu, dtype=torch.float32, device="cuda")
+    n = torch.as_tensor(nu, dtype=torch.float32, device="cuda")
+    s = B.BfmSolver(m, n, tol=0.0, max_iter=10)
+    s.iterate(10)
+    r = s.finish(with_map=False)
+    torch.cuda.synchronize()
+    assert r["iters"] == 10
+    return dict(mu=mu, nu=nu, mu32=m, nu32=n, phi=r["phi"].double().cpu().numpy(),
+                psi_dev=r["psi"], psi=r["psi"].double().cpu().numpy())
+
+
+def test_full_size_psi_whole_field(ten):
+    want = oracle.ctransform(ten["phi"], "linear")
+    scale = 1.0 + np.max(np.abs(ten["phi"]))
+    err = np.max(np.abs(ten["psi"] - want))
+    assert err <= 4 * np.finfo(np.float32).eps * scale, err
+
+
+def test_full_size_pushforward_whole_field(B, ten):
+    rho = B.bfm_pushforward(ten["psi_dev"], ten["mu32"])
+    torch.cuda.synchronize()
+    got = rho.double().cpu().numpy()
+    want = oracle.pushforward(ten["psi"], ten["mu32"].double().cpu().numpy())
+    err = np.max(np.abs(got - want))
+    assert err <= 2e-5 * np.max(want), (err, np.max(want))
+    ten["rho_dev"] = rho
+
+
+def test_full_size_poisson_whole_field(B, ten):
+    rho = ten.get("rho_dev")
+    if rho is None:
+        rho = B.bfm_pushforward(ten["psi_dev"], ten["mu32"])
+    f = (ten["nu32"] - rho).contiguous()
+    g, G = B.bfm_poisson(f)
+    torch.cuda.synchronize()
+    g_want, G_want = oracle.poisson(f.double().cpu().numpy(), "fft")
+    err = np.max(np.abs(g.double().cpu().numpy() - g_want))
+    assert err <= 2e-5 * np.max(np.abs(g_want)), (err, np.max(np.abs(g_want)))
+    assert abs(G - G_want) <= 2e-5 * abs(G_want), (G, G_want)
