@@ -286,7 +286,10 @@ bfm_status bfm_poisson(const void *f, void *g, const bfm_grid *grid, bfm_precisi
  * device address; make that first call before any stream capture begins.
  * Every call on a device uses the same array: calls whose GPU work overlaps
  * (different streams or host threads) race and must be serialised by the
- * caller.
+ * caller.  The looked-up address is kept per device for the life of the
+ * process; cudaDeviceReset rebuilds the device's context and module, after
+ * which the kept address is stale, so do not call this entry point on a
+ * device after resetting it.
  */
 bfm_status bfm_poisson_noalloc(const void *f, void *g, const bfm_grid *grid, bfm_precision prec,
                                double *G_out, void *stream);
@@ -334,6 +337,58 @@ bfm_status bfm_pushforward(const void *psi, const void *mu, void *rho, const bfm
  */
 bfm_status bfm_interpolate(const void *map, const void *mu, double t, void *rho,
                            const bfm_grid *grid, bfm_precision prec, void *stream);
+
+/*
+ * Launch shapes of the line c-transform (Section 4.1 computes the transform
+ * line by line; here a thread takes K consecutive cells of a line and a CTA
+ * W lines) and the autotuner that chooses them by timing.  The paper has no
+ * counterpart: its transform is a sequential sweep.  Kinds of line kernel
+ * (kind): 0 = tile rows (axis 0, lines of at most 256 cells), 1 = tile
+ * columns (axes > 0, W neighbouring lines interleaved), 2 = the row kernel
+ * (axis 0, rows of more than 256 cells).  A shape is (K, W) with W = 0 for
+ * "as many lines as fit" (512 threads, about 110 KB of shared memory).
+ * Every shape computes the same exact discrete envelope; shapes differ in
+ * speed only (and in rounding order where hidden-parabola tests tie).
+ * The table of chosen shapes is process-wide, read whenever a pass is
+ * planned (bfm_solve captures its plan once per call); set shapes before a
+ * solve starts, not while one runs in another thread.
+ *
+ * bfm_tune_candidates: the shapes the tuner tries for lines of n cells of
+ *   this kind, into K[i], W[i] (HOST, cap entries; may be NULL to count).
+ *   Returns their number, or -1 for an unknown kind or n < 2.
+ * bfm_tune_default: the hand-picked shape (-1 as above).
+ * bfm_tune_set: store a shape (BFM_ERR_INVALID_ARG unless it is a candidate).
+ * bfm_tune_get: the shape plans take now; returns 1 if stored, 0 if default.
+ * bfm_tune_clear: forget every stored shape.
+ * bfm_tune_pick: the tuner's choice among timings ms[0..ncand) (ms <= 0:
+ *   not measured): the fastest, unless the default (default_index, or -1)
+ *   is within a factor 1 + margin of it, when the default stays.
+ * bfm_tune_passes: the (kind, n) pairs the c-transforms of a solve on this
+ *   grid read (batched != 0: of the batched solver), into kinds[i], ns[i]
+ *   (HOST, cap entries); returns their number, -1 for an unsupported grid.
+ * bfm_autotune_scratch_bytes: device scratch bfm_autotune needs (two fields
+ *   of about 8 M cells of lines of n cells), 0 for an unknown kind or n.
+ * bfm_autotune: time every candidate of (kind, n) on a synthetic field in
+ *   `scratch` (DEVICE, caller-owned, 256-byte aligned, at least
+ *   bfm_autotune_scratch_bytes) on `stream` (CUDA events, median of five
+ *   launches after two untimed ones), store the pick (margin 2%) and return
+ *   it in K_out, W_out (HOST, may be NULL); ms_out (HOST, may be NULL)
+ *   receives up to ms_cap candidate times in the order of
+ *   bfm_tune_candidates.  Synchronises the stream.  Errors:
+ *   BFM_ERR_INVALID_ARG (kind/n), BFM_ERR_WORKSPACE (scratch), BFM_ERR_CUDA;
+ *   on an error the table entry of (kind, n) is left as it was.
+ */
+int bfm_tune_candidates(int kind, int n, bfm_precision prec, int *K, int *W, int cap);
+int bfm_tune_default(int kind, int n, bfm_precision prec, int *K, int *W);
+bfm_status bfm_tune_set(int kind, int n, bfm_precision prec, int K, int W);
+int bfm_tune_get(int kind, int n, bfm_precision prec, int *K, int *W);
+void bfm_tune_clear(void);
+int bfm_tune_pick(const double *ms, int ncand, int default_index, double margin);
+int bfm_tune_passes(const bfm_grid *grid, bfm_precision prec, int batched, int *kinds, int *ns,
+                    int cap);
+size_t bfm_autotune_scratch_bytes(int kind, int n, bfm_precision prec);
+bfm_status bfm_autotune(int kind, int n, bfm_precision prec, void *scratch, size_t scratch_bytes,
+                        void *stream, int *K_out, int *W_out, double *ms_out, int ms_cap);
 
 #ifdef __cplusplus
 }

@@ -115,6 +115,25 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_double), _P,
                                        ctypes.POINTER(ctypes.c_void_p),
                                        ctypes.POINTER(ctypes.c_void_p), _P, ctypes.c_size_t, _P]),
+    "bfm_tune_candidates": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "bfm_tune_default": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "bfm_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int]),
+    "bfm_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "bfm_tune_clear": (None, []),
+    "bfm_tune_pick": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double]),
+    "bfm_tune_passes": (ctypes.c_int, [_GP, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.c_int]),
+    "bfm_autotune_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "bfm_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t,
+                                    _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "bfm_profile_kinds": (ctypes.c_int, []),
     "bfm_profile_kind_name": (ctypes.c_char_p, [ctypes.c_int]),
     "bfm_profile_begin": (ctypes.c_int, [ctypes.c_int]),
@@ -485,6 +504,97 @@ class BfmSolver:
                     max_mu=res.max_mu, max_nu=res.max_nu)
 
 
+# --- launch shapes of the line c-transform (autotuner) -------------------------
+
+CT_KIND_TILE_ROWS, CT_KIND_TILE_COLS, CT_KIND_ROW = 0, 1, 2
+CT_KIND_NAMES = {0: "tile_rows", 1: "tile_cols", 2: "row"}
+
+
+def _prec_of_dtype(dtype) -> int:
+    import torch
+    return BFM_FP64 if dtype in (torch.float64, np.float64) else BFM_FP32
+
+
+def bfm_tune_candidates(kind: int, n: int, prec: int = BFM_FP32) -> list:
+    """The (K cells per thread, W lines per CTA; 0 = as many as fit) shapes
+    the tuner tries for lines of n cells taking kernel `kind`."""
+    m = lib().bfm_tune_candidates(kind, n, prec, None, None, 0)
+    if m < 0:
+        raise ValueError("unknown kernel kind or line length")
+    K = (ctypes.c_int * max(m, 1))()
+    W = (ctypes.c_int * max(m, 1))()
+    lib().bfm_tune_candidates(kind, n, prec, K, W, m)
+    return [(K[i], W[i]) for i in range(m)]
+
+
+def bfm_tune_default(kind: int, n: int, prec: int = BFM_FP32) -> tuple:
+    K, W = ctypes.c_int(), ctypes.c_int()
+    if lib().bfm_tune_default(kind, n, prec, ctypes.byref(K), ctypes.byref(W)) < 0:
+        raise ValueError("unknown kernel kind or line length")
+    return K.value, W.value
+
+
+def bfm_tune_set(kind: int, n: int, K: int, W: int, prec: int = BFM_FP32) -> None:
+    _check(lib().bfm_tune_set(kind, n, prec, K, W), "bfm_tune_set")
+
+
+def bfm_tune_get(kind: int, n: int, prec: int = BFM_FP32) -> tuple:
+    """(K, W, tuned): the shape plans take now, and whether it was stored."""
+    K, W = ctypes.c_int(), ctypes.c_int()
+    t = lib().bfm_tune_get(kind, n, prec, ctypes.byref(K), ctypes.byref(W))
+    return K.value, W.value, bool(t)
+
+
+def bfm_tune_clear() -> None:
+    lib().bfm_tune_clear()
+
+
+def bfm_tune_pick(ms, default_index: int, margin: float = 0.02) -> int:
+    a = (ctypes.c_double * len(ms))(*[float(v) for v in ms])
+    return lib().bfm_tune_pick(a, len(ms), default_index, margin)
+
+
+def bfm_tune_passes(shape, prec: int = BFM_FP32, batched: bool = False) -> list:
+    """The (kind, n) pairs whose shapes the c-transforms of a solve on this
+    grid read (batched: the batched solver's passes)."""
+    g = grid_of(shape)
+    K = (ctypes.c_int * 6)()
+    N = (ctypes.c_int * 6)()
+    m = lib().bfm_tune_passes(ctypes.byref(g), prec, int(batched), K, N, 6)
+    if m < 0:
+        raise ValueError("unsupported grid")
+    return [(K[i], N[i]) for i in range(m)]
+
+
+def bfm_autotune(kind: int, n: int, prec: int = BFM_FP32, device=None) -> dict:
+    """Time every candidate shape of kernel `kind` on lines of n cells and
+    store the fastest for this process (bfm_autotune in include/bfm.h).
+    Scratch comes from torch here; the library allocates nothing."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    nb = lib().bfm_autotune_scratch_bytes(kind, n, prec)
+    if nb == 0:
+        raise ValueError("unknown kernel kind or line length")
+    buf = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+    p = (buf.data_ptr() + 255) & ~255
+    cand = bfm_tune_candidates(kind, n, prec)
+    ms = (ctypes.c_double * len(cand))()
+    K, W = ctypes.c_int(), ctypes.c_int()
+    _check(lib().bfm_autotune(kind, n, prec, p, nb, _stream(), ctypes.byref(K), ctypes.byref(W),
+                              ms, len(cand)), "bfm_autotune")
+    del buf
+    return {"kind": CT_KIND_NAMES[kind], "n": n, "K": K.value, "W": W.value,
+            "default": bfm_tune_default(kind, n, prec),
+            "candidates": [{"K": c[0], "W": c[1], "ms": ms[i]} for i, c in enumerate(cand)]}
+
+
+def autotune_grid(shape, dtype=None, batched: bool = False) -> list:
+    """Tune every (kind, n) the c-transforms of a solve on this grid take."""
+    import torch
+    prec = _prec_of_dtype(dtype if dtype is not None else torch.float32)
+    return [bfm_autotune(k, n, prec) for (k, n) in bfm_tune_passes(shape, prec, batched)]
+
+
 def bfm_profile_begin(max_records: int = 4096):
     _check(lib().bfm_profile_begin(int(max_records)), "bfm_profile_begin")
 
@@ -509,14 +619,25 @@ def _ptr_array(tensors):
 
 
 def bfm_solve_batched(mus, nus, tol: float = 1e-4, max_iter: int = 500, with_map: bool = False,
-                      **opts) -> list:
+                      autotune: bool = False, **opts) -> list:
     """Independent problems of uneven grid sizes solved together (one batched
     launch per kernel step and grid shape, per-problem convergence).  `mus`,
-    `nus`: lists of CUDA tensors (same dtype).  Returns one dict per problem."""
+    `nus`: lists of CUDA tensors (same dtype).  autotune: first time the
+    c-transform's launch shapes for every line length of the batch that has
+    no stored shape yet (bfm_autotune).  Returns one dict per problem."""
     import torch
     n = len(mus)
     if n == 0 or len(nus) != n:
         raise ValueError("mus and nus must be non-empty lists of equal length")
+    if autotune:
+        prec0 = _prec(mus[0])
+        todo = set()
+        for m in mus:
+            for kind, ln in bfm_tune_passes(tuple(m.shape), prec0, batched=True):
+                if not bfm_tune_get(kind, ln, prec0)[2]:
+                    todo.add((kind, ln))
+        for kind, ln in sorted(todo):
+            bfm_autotune(kind, ln, prec0, device=mus[0].device)
     prec = _prec(mus[0])
     grids = (bfm_grid * n)()
     results = (bfm_result * n)()

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbfm.so")
 SOURCES = ["common.cu", "ctransform.cu", "ctpower.cu", "dct.cu", "scatter.cu", "layout.cu",
-           "solver.cu", "noalloc.cu", "batched.cu"]
+           "solver.cu", "noalloc.cu", "batched.cu", "autotune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xptxas", "-warn-spills"]

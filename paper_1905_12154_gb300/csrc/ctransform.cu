@@ -24,6 +24,9 @@
 // load and store sweeps and written as one partial sum per CTA.
 #include <string.h>
 
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -1235,11 +1238,13 @@ void* select_kernel(int K, bool contig, bool batched)
 
 }  // namespace
 
-CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
+// Tile plan with K cells per thread and (Wreq > 0) at most Wreq lines per
+// CTA; Wreq <= 0 takes as many lines as the thread and memory limits allow.
+static CtPlan plan_ct_tile(const Grid& g, int axis, int elem_bytes, int K, int Wreq)
 {
     CtPlan p;
     const int n = g.n[axis];
-    p.K = pick_K(n);
+    p.K = K;
     p.G = next_pow2((n + p.K - 1) / p.K);
     const bool contig = (axis == 0);
     // pad words of the skewed layout: one per 2^lg cells (Skew<K>: lg = log2 of
@@ -1261,6 +1266,7 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
     if (W > 32) W = 32;
     const size_t budget = 110 * 1024;
     while (W > 1 && (size_t)W * line_bytes > budget) --W;
+    if (Wreq > 0 && W > Wreq) W = Wreq;
     if (!contig) {
         // interleaved tiles: W a power of two (division-free index math)
         int p2 = 1;
@@ -1294,11 +1300,11 @@ static bool use_row_kernel(const Grid& g, int axis) { return axis == 0 && g.n[0]
 // Row kernel plan: K = 32 or 16 cells per thread, G = the next power of two
 // of n / K (at least 32 for n > 256, so every group is whole warps), as many
 // groups per CTA as fit 512 threads and about 110 KB (two CTAs per SM).
-static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
+static CtPlan plan_ct_row_shape(const Grid& g, int elem_bytes, int K, int Wreq)
 {
     CtPlan p;
     const int n = g.n[0];
-    p.K = row_cells_per_thread(n);
+    p.K = K;
     p.G = next_pow2((n + p.K - 1) / p.K);
     const int chunks = (n + p.K - 1) / p.K + 1;
     p.LD = n + chunks + 2;
@@ -1314,6 +1320,7 @@ static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
     int W = 512 / p.G;
     if (W < 1) W = 1;
     while (W > 1 && (size_t)W * line_bytes > 110 * 1024) --W;
+    if (Wreq > 0 && W > Wreq) W = Wreq;
     p.W = W;
     size_t off = (size_t)W * p.LD * elem_bytes + (size_t)W * p.LDI * 2 + (size_t)W * 3 * p.G * 2;
     off = (off + 15) & ~(size_t)15;
@@ -1323,6 +1330,155 @@ static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
     p.threads = W * p.G;
     p.tiles = make_tiles(g, 0, W);
     return p;
+}
+
+// ---------------------------------------------------------------------------
+// launch shapes and the tuning table
+// ---------------------------------------------------------------------------
+// A pass's shape is (K cells per thread, W lines per CTA) of its kernel kind:
+// tile rows (axis 0, lines of at most 256 cells), tile columns (axes > 0:
+// W neighbouring lines interleaved) or the row kernel (axis 0, rows of more
+// than 256 cells).  The default shapes are the hand-picked ones; the
+// autotuner (bfm_autotune) times the candidates of a line length and stores
+// the fastest here, and every later plan of that kind and length takes it.
+// Any candidate gives the same envelope (the same exact-discrete transform),
+// so a tuned shape changes timing, not results beyond rounding order.
+int ct_kind(const Grid& g, int axis)
+{
+    if (use_row_kernel(g, axis)) return CT_KIND_ROW;
+    return axis == 0 ? CT_KIND_TILE_ROWS : CT_KIND_TILE_COLS;
+}
+
+CtShape ct_default_shape(int kind, int n, int elem_bytes)
+{
+    (void)elem_bytes;
+    if (kind == CT_KIND_ROW) return CtShape{row_cells_per_thread(n), 0};
+    return CtShape{pick_K(n), 0};
+}
+
+static bool tile_K_ok(int n, int K)
+{
+    if (K != 1 && K != 2 && K != 4 && K != 8 && K != 12 && K != 16) return false;
+    if (K > n) return false;
+    if (K == 12 && n % 12 != 0) return false;
+    return next_pow2((n + K - 1) / K) <= 512;
+}
+
+static bool row_K_ok(int n, int K)
+{
+    if (n <= kRowMinN || (K != 16 && K != 32)) return false;
+    const int G = next_pow2((n + K - 1) / K);
+    return G >= 32 && G <= 512;
+}
+
+// the lines per CTA a plan with this K takes when unrestricted
+static int max_lines(int kind, int n, int elem_bytes, int K)
+{
+    int dims[3] = {n, 64, 1};
+    if (kind == CT_KIND_TILE_COLS) { dims[0] = 64; dims[1] = n; }
+    bfm_grid bg{2, {dims[0], dims[1], 1}};
+    Grid g;
+    make_grid(&bg, &g);
+    if (kind == CT_KIND_ROW) return plan_ct_row_shape(g, elem_bytes, K, 0).W;
+    return plan_ct_tile(g, kind == CT_KIND_TILE_COLS ? 1 : 0, elem_bytes, K, 0).W;
+}
+
+int ct_shape_candidates(int kind, int n, int elem_bytes, CtShape* out, int cap)
+{
+    static const int tileK[] = {1, 2, 4, 8, 12, 16};
+    static const int rowK[] = {16, 32};
+    const int* Ks = kind == CT_KIND_ROW ? rowK : tileK;
+    const int nK = kind == CT_KIND_ROW ? 2 : 6;
+    int cnt = 0;
+    for (int i = 0; i < nK; ++i) {
+        const int K = Ks[i];
+        if (kind == CT_KIND_ROW ? !row_K_ok(n, K) : !tile_K_ok(n, K)) continue;
+        const int Wm = max_lines(kind, n, elem_bytes, K);
+        const int G = next_pow2((n + K - 1) / K);
+        // the unrestricted W and up to two halvings of it, keeping CTAs of
+        // whole warps (lines shorter than a warp fill it)
+        for (int W = Wm, k = 0; W >= 1 && k < 3; W = (W > 1 ? W / 2 : 0), ++k) {
+            if (W * G < 32 || (G < 32 && (W * G) % 32 != 0)) break;
+            if (cnt < cap && out) out[cnt] = CtShape{K, W == Wm ? 0 : W};
+            ++cnt;
+            if (W == 1) break;
+        }
+    }
+    return cnt;
+}
+
+bool ct_shape_valid(int kind, int n, int elem_bytes, CtShape s)
+{
+    CtShape c[64];
+    const int m = ct_shape_candidates(kind, n, elem_bytes, c, 64);
+    for (int i = 0; i < m && i < 64; ++i)
+        if (c[i].K == s.K && c[i].W == s.W) return true;
+    return false;
+}
+
+namespace {
+struct TuneKey {
+    int kind, n, elem;
+    bool operator<(const TuneKey& o) const
+    {
+        if (kind != o.kind) return kind < o.kind;
+        if (n != o.n) return n < o.n;
+        return elem < o.elem;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, CtShape> g_tune;
+}  // namespace
+
+bool ct_tuned_shape(int kind, int n, int elem_bytes, CtShape* s)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(TuneKey{kind, n, elem_bytes});
+    if (it == g_tune.end()) return false;
+    *s = it->second;
+    return true;
+}
+
+void ct_set_tuned_shape(int kind, int n, int elem_bytes, CtShape s)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[TuneKey{kind, n, elem_bytes}] = s;
+}
+
+void ct_erase_tuned_shape(int kind, int n, int elem_bytes)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.erase(TuneKey{kind, n, elem_bytes});
+}
+
+void ct_clear_tuned_shapes()
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+}
+
+static CtShape shape_for(int kind, int n, int elem_bytes)
+{
+    CtShape s;
+    if (ct_tuned_shape(kind, n, elem_bytes, &s)) return s;
+    return ct_default_shape(kind, n, elem_bytes);
+}
+
+CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
+{
+    const CtShape s = shape_for(axis == 0 ? CT_KIND_TILE_ROWS : CT_KIND_TILE_COLS, g.n[axis], elem_bytes);
+    return plan_ct_tile(g, axis, elem_bytes, s.K, s.W);
+}
+
+CtPlan plan_ct_pass_default(const Grid& g, int axis, int elem_bytes)
+{
+    return plan_ct_tile(g, axis, elem_bytes, pick_K(g.n[axis]), 0);
+}
+
+static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
+{
+    const CtShape s = shape_for(CT_KIND_ROW, g.n[0], elem_bytes);
+    return plan_ct_row_shape(g, elem_bytes, s.K, s.W);
 }
 
 template <typename T>

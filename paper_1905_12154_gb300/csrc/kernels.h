@@ -35,7 +35,21 @@ struct DctPlan {
     LineTiles tiles;
 };
 
-CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes);
+// c-transform launch shapes: K cells per thread, W lines per CTA (0: as many
+// as the thread and shared-memory limits allow), per kernel kind
+enum { CT_KIND_TILE_ROWS = 0, CT_KIND_TILE_COLS = 1, CT_KIND_ROW = 2 };
+struct CtShape { int K, W; };
+int ct_kind(const Grid& g, int axis);
+CtShape ct_default_shape(int kind, int n, int elem_bytes);
+int ct_shape_candidates(int kind, int n, int elem_bytes, CtShape* out, int cap);
+bool ct_shape_valid(int kind, int n, int elem_bytes, CtShape s);
+bool ct_tuned_shape(int kind, int n, int elem_bytes, CtShape* s);
+void ct_set_tuned_shape(int kind, int n, int elem_bytes, CtShape s);
+void ct_erase_tuned_shape(int kind, int n, int elem_bytes);
+void ct_clear_tuned_shapes();
+
+CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes);          // tuned shape, else default
+CtPlan plan_ct_pass_default(const Grid& g, int axis, int elem_bytes);  // hand-picked shape
 DctPlan plan_dct_pass(const Grid& g, int axis, int elem_bytes);
 
 // number of CTAs (= partial sums) launch_ct_pass uses for this pass

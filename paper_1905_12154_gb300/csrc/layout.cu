@@ -174,7 +174,7 @@ bool transposed_axis1(const Grid& g, int elem_bytes)
 {
     // a column tile narrower than 8 lines moves less than one 32-byte sector
     // of FP32 per row
-    return g.ndim == 2 && plan_ct_pass(g, 1, elem_bytes).W < 8;
+    return g.ndim == 2 && plan_ct_pass_default(g, 1, elem_bytes).W < 8;
 }
 
 Grid transposed_grid(const Grid& g)
