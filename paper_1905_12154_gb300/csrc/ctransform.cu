@@ -6,17 +6,27 @@
 //     u(i) = min_j  hh (i - j)^2 + f(j),     hh = h^2 / 2,
 // i.e. the lower envelope of n parabolas of equal curvature.  The paper
 // evaluates it through the Legendre transform and a convex-hull sweep; here
-// the same envelope is built in parallel inside one CTA per line tile:
+// the same envelope is built in parallel by a thread group per line (a CTA
+// holds several lines):
 //   A. each thread builds the envelope of its own K consecutive parabolas
-//      with a stack (a parabola b between a and c is hidden when the a/b
-//      crossing lies right of the b/c crossing);
-//   B. neighbouring envelopes are merged pairwise in log2(G) rounds: two
-//      envelopes whose parabolas are separated meet at one crossover, so the
-//      merge keeps a prefix of the left one and a suffix of the right one,
-//      found by popping hidden ends (the lower common tangent walk);
-//   C. the surviving parabolas are compacted with a prefix sum;
-//   D. each thread finds the parabola owning its first output cell by binary
-//      search and sweeps its K outputs monotonically.
+//      with a stack kept in place over its cells (a parabola b between a and
+//      c is hidden when the a/b crossing lies right of the b/c crossing);
+//   B. the chunk envelopes are joined by rounds: a parabola is on the line's
+//      envelope iff its lifted point is on the lower convex hull, and in the
+//      concatenation of the chunk stacks only stack ends can be reflex, so in
+//      a round every thread drops the first entries that lie on or above the
+//      chord from the left neighbour's last entry and the last entries on or
+//      above the chord to the right neighbour's first (each boundary by one
+//      direct test and a binary search); rounds repeat until none drops, a
+//      line still changing after a fixed number of rounds finishes with
+//      pairwise merges of neighbouring stacks;
+//   C. the non-empty stacks are listed in order (the tile kernel compacts
+//      the surviving parabolas into one list);
+//   D. FP32: every envelope parabola computes the first cell it owns from its
+//      predecessor; the row kernel finds each cell's owner by the rank of the
+//      owners' start cells, the tile kernel by marks at the start cells; FP64
+//      lines, and lines whose start cells decrease under rounding, find the
+//      owner of a thread's first cell by binary search and sweep its outputs.
 // The division-free hidden test compares second differences:
 //   b hidden by (a, c)  <=>  (f_b-f_a)(c-b) - (f_c-f_b)(b-a) >= hh (c-a)(b-a)(c-b).
 // Optional FP64 dot products of the input and of the output with weight
