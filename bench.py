@@ -68,14 +68,14 @@ def transpose_bytes_per_cell(launches_per_iter: float) -> float:
 # solve, whose summary sits under profiles/); reported only while the
 # kernel source still matches the one the counters were taken on
 TRAFFIC = {
-    # second sweeps (rows of a transposed field, no dot): launches 1 and 11 of the capture
-    "ct_pass_axis1": {"bytes": (67174912 + 11891456 + 67174912 + 11732480) / 2,
+    # second sweeps (rows of a transposed field, no dot): mean of 5 launches
+    "ct_pass_axis1": {"bytes": 67175577.6 + 11713536.0,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "4ca2650b47880c195bb496ce11075cd5a94337229e356722f787fa6d2d6d31be"},
-    # first sweeps (with the dual dot on load): launches 9 and 12
-    "ct_pass_axis0": {"bytes": (134398464 + 25198592 + 135450368 + 27258624) / 2,
+                      "sha256": "aa1b97b73ffd6cdea77781c0c2e3e9dd675db80c12c42d320032017c42bba6b9"},
+    # first sweeps (with the dual dot on load): mean of 4 launches
+    "ct_pass_axis0": {"bytes": 134847936.0 + 25598976.0,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "4ca2650b47880c195bb496ce11075cd5a94337229e356722f787fa6d2d6d31be"},
+                      "sha256": "aa1b97b73ffd6cdea77781c0c2e3e9dd675db80c12c42d320032017c42bba6b9"},
 }
 
 
