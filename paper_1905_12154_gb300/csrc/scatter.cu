@@ -241,7 +241,21 @@ __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restri
     const int n0 = g.n[0];
     const long long rows = g.N / n0;
     const unsigned items = (unsigned)(rows * per_row);     // < 2^31 (checked by the launcher)
-    for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+    const unsigned stride = gridDim.x * blockDim.x;
+    // the source density of the thread's next item is loaded while the current
+    // one is processed (its psi loads wait for it otherwise)
+    VT mv[NV];
+    auto load_mu = [&](unsigned it) {
+        const unsigned row = it / (unsigned)per_row;
+        const int x0 = (int)(it - row * (unsigned)per_row) * CW;
+        const long long base = (long long)row * n0 + x0;
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+            if (j == 0 || x0 + j * V < n0) mv[j] = *reinterpret_cast<const VT*>(mu + base + j * V);
+    };
+    unsigned it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it < items) load_mu(it);
+    for (; it < items; it += stride) {
         const unsigned row = it / (unsigned)per_row;
         const int x0 = (int)(it - row * (unsigned)per_row) * CW;
         const long long base = (long long)row * n0 + x0;
@@ -249,11 +263,12 @@ __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restri
         bool any = false;
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            if (j == 0 || x0 + j * V < n0) unpack<T>(*reinterpret_cast<const VT*>(mu + base + j * V), m + j * V);
+            if (j == 0 || x0 + j * V < n0) unpack<T>(mv[j], m + j * V);
             else
 #pragma unroll
                 for (int k = 0; k < V; ++k) m[j * V + k] = (T)0;
         }
+        if (it + stride < items) load_mu(it + stride);
 #pragma unroll
         for (int k = 0; k < CW; ++k) any |= (m[k] != (T)0);
         if (!any) continue;
