@@ -908,11 +908,27 @@ dct_row_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
             }
         }
         __syncthreads();
-        if (MODE != DCT_INV) {
-            if (MODE == DCT_MID) fft_fixed_call<-1, LOGN>(z, t, a.ptw);
-            else fft_fixed<-1, LOGN>(z, t, a.ptw);
-            // DCT-II from the FFT of the pair (Makhoul): split the two real
-            // lines' spectra, then twiddle by e^{-i pi k/(2n)}
+        if (MODE == DCT_MID) {
+            fft_fixed_call<-1, LOGN>(z, t, a.ptw);
+            // One pass over the pairs (k, n - k): the DCT-II of both lines from
+            // the pair's FFT (Makhoul), the division by lambda(row) + lambda(k)
+            // with G = sum w |f^|^2 / lambda (Parseval weights 1, 2; zero mode
+            // -> 0), and the inverse twiddle and recombination that feed the
+            // inverse FFT -- the arithmetic of the three separate loops of the
+            // other passes, without their shared-memory round trips.
+            const long long ia = ra, ib = ra + 1;
+            const float La = a.lam_a0[ia], Lb = hb ? a.lam_a0[ib] : 0.f;
+            const float wa = (ia == 0) ? 1.f : 2.f, wb = 2.f;
+            auto divide = [&](int kk, C v) {
+                const float lk = a.lam_axis[kk];
+                const float wk = (kk == 0) ? 1.f : 2.f;
+                const float la = La + lk, lb = Lb + lk;
+                float ga = 0.f, gb = 0.f;
+                if (la > 0.f) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
+                if (hb && lb > 0.f) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
+                v.x = ga; v.y = gb;
+                return v;
+            };
             for (int k = t; k <= n / 2; k += T) {
                 const int km = (n - k) & (n - 1);
                 const C Zk = z[padix(k)], Zm = z[padix(km)];
@@ -921,61 +937,105 @@ dct_row_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
                 Bq.x = 0.5f * (Zk.y + Zm.y); Bq.y = 0.5f * (Zm.x - Zk.x);
                 const C dk = a.dtw[k];
                 C outk; outk.x = dk.x * A.x - dk.y * A.y; outk.y = dk.x * Bq.x - dk.y * Bq.y;
+                const C Xk = divide(k, outk);
+                C Xm = Xk;
+                const C dm = a.dtw[km];
                 if (km != k) {
                     C Am, Bm;
                     Am.x = 0.5f * (Zm.x + Zk.x); Am.y = 0.5f * (Zm.y - Zk.y);
                     Bm.x = 0.5f * (Zm.y + Zk.y); Bm.y = 0.5f * (Zk.x - Zm.x);
-                    const C dm = a.dtw[km];
                     C outm; outm.x = dm.x * Am.x - dm.y * Am.y; outm.y = dm.x * Bm.x - dm.y * Bm.y;
-                    z[padix(km)] = outm;
+                    Xm = divide(km, outm);
                 }
-                z[padix(k)] = outk;
-            }
-            __syncthreads();
-        }
-        if (MODE == DCT_MID) {
-            // divide by the eigenvalue lambda(row) + lambda(k) (zero mode -> 0)
-            // and accumulate G = sum w |f^|^2 / lambda (Parseval weights 1, 2)
-            const long long ia = ra, ib = ra + 1;
-            const float La = a.lam_a0[ia], Lb = hb ? a.lam_a0[ib] : 0.f;
-            const float wa = (ia == 0) ? 1.f : 2.f, wb = 2.f;
-            for (int k = t; k < n; k += T) {
-                const float lk = a.lam_axis[k];
-                const float wk = (k == 0) ? 1.f : 2.f;
-                C v = z[padix(k)];
-                const float la = La + lk, lb = Lb + lk;
-                float ga = 0.f, gb = 0.f;
-                if (la > 0.f) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
-                if (hb && lb > 0.f) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
-                v.x = ga; v.y = gb;
-                z[padix(k)] = v;
+                const float xam = (k == 0) ? 0.f : Xm.x, xbm = (k == 0) ? 0.f : Xm.y;
+                const C dki = cconj(dk);
+                C Va, Vb;
+                Va.x = dki.x * Xk.x + dki.y * xam; Va.y = dki.y * Xk.x - dki.x * xam;
+                Vb.x = dki.x * Xk.y + dki.y * xbm; Vb.y = dki.y * Xk.y - dki.x * xbm;
+                C Zk2; Zk2.x = Va.x - Vb.y; Zk2.y = Va.y + Vb.x;
+                if (km != k) {
+                    const C dmi = cconj(dm);
+                    C Wa, Wb;
+                    Wa.x = dmi.x * Xm.x + dmi.y * Xk.x; Wa.y = dmi.y * Xm.x - dmi.x * Xk.x;
+                    Wb.x = dmi.x * Xm.y + dmi.y * Xk.y; Wb.y = dmi.y * Xm.y - dmi.x * Xk.y;
+                    C Zm2; Zm2.x = Wa.x - Wb.y; Zm2.y = Wa.y + Wb.x;
+                    z[padix(km)] = Zm2;
+                }
+                z[padix(k)] = Zk2;
             }
             acc += gsum.take();
             __syncthreads();
-        }
-        if (MODE != DCT_FWD) {
-            // undo the DCT-II twiddle and recombine the pair's spectra
-            for (int k = t; k <= n / 2; k += T) {
-                const int km = (n - k) & (n - 1);
-                const C Xk = z[padix(k)], Xm = z[padix(km)];
-                const float xam = (k == 0) ? 0.f : Xm.x, xbm = (k == 0) ? 0.f : Xm.y;
-                const C dk = cconj(a.dtw[k]);
-                C Va, Vb;
-                Va.x = dk.x * Xk.x + dk.y * xam; Va.y = dk.y * Xk.x - dk.x * xam;
-                Vb.x = dk.x * Xk.y + dk.y * xbm; Vb.y = dk.y * Xk.y - dk.x * xbm;
-                C Zk; Zk.x = Va.x - Vb.y; Zk.y = Va.y + Vb.x;
-                if (km != k) {
-                    const C dm = cconj(a.dtw[km]);
-                    C Wa, Wb;
-                    Wa.x = dm.x * Xm.x + dm.y * Xk.x; Wa.y = dm.y * Xm.x - dm.x * Xk.x;
-                    Wb.x = dm.x * Xm.y + dm.y * Xk.y; Wb.y = dm.y * Xm.y - dm.x * Xk.y;
-                    C Zm; Zm.x = Wa.x - Wb.y; Zm.y = Wa.y + Wb.x;
-                    z[padix(km)] = Zm;
-                }
-                z[padix(k)] = Zk;
-            }
-            __syncthreads();
             fft_fixed_call<+1, LOGN>(z, t, a.ptw);
+        } else {
+        if (MODE != DCT_INV) {
+                if (MODE == DCT_MID) fft_fixed_call<-1, LOGN>(z, t, a.ptw);
+                else fft_fixed<-1, LOGN>(z, t, a.ptw);
+                // DCT-II from the FFT of the pair (Makhoul): split the two real
+                // lines' spectra, then twiddle by e^{-i pi k/(2n)}
+                for (int k = t; k <= n / 2; k += T) {
+                    const int km = (n - k) & (n - 1);
+                    const C Zk = z[padix(k)], Zm = z[padix(km)];
+                    C A, Bq;
+                    A.x = 0.5f * (Zk.x + Zm.x); A.y = 0.5f * (Zk.y - Zm.y);
+                    Bq.x = 0.5f * (Zk.y + Zm.y); Bq.y = 0.5f * (Zm.x - Zk.x);
+                    const C dk = a.dtw[k];
+                    C outk; outk.x = dk.x * A.x - dk.y * A.y; outk.y = dk.x * Bq.x - dk.y * Bq.y;
+                    if (km != k) {
+                        C Am, Bm;
+                        Am.x = 0.5f * (Zm.x + Zk.x); Am.y = 0.5f * (Zm.y - Zk.y);
+                        Bm.x = 0.5f * (Zm.y + Zk.y); Bm.y = 0.5f * (Zk.x - Zm.x);
+                        const C dm = a.dtw[km];
+                        C outm; outm.x = dm.x * Am.x - dm.y * Am.y; outm.y = dm.x * Bm.x - dm.y * Bm.y;
+                        z[padix(km)] = outm;
+                    }
+                    z[padix(k)] = outk;
+                }
+                __syncthreads();
+            }
+            if (MODE == DCT_MID) {
+                // divide by the eigenvalue lambda(row) + lambda(k) (zero mode -> 0)
+                // and accumulate G = sum w |f^|^2 / lambda (Parseval weights 1, 2)
+                const long long ia = ra, ib = ra + 1;
+                const float La = a.lam_a0[ia], Lb = hb ? a.lam_a0[ib] : 0.f;
+                const float wa = (ia == 0) ? 1.f : 2.f, wb = 2.f;
+                for (int k = t; k < n; k += T) {
+                    const float lk = a.lam_axis[k];
+                    const float wk = (k == 0) ? 1.f : 2.f;
+                    C v = z[padix(k)];
+                    const float la = La + lk, lb = Lb + lk;
+                    float ga = 0.f, gb = 0.f;
+                    if (la > 0.f) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
+                    if (hb && lb > 0.f) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
+                    v.x = ga; v.y = gb;
+                    z[padix(k)] = v;
+                }
+                acc += gsum.take();
+                __syncthreads();
+            }
+            if (MODE != DCT_FWD) {
+                // undo the DCT-II twiddle and recombine the pair's spectra
+                for (int k = t; k <= n / 2; k += T) {
+                    const int km = (n - k) & (n - 1);
+                    const C Xk = z[padix(k)], Xm = z[padix(km)];
+                    const float xam = (k == 0) ? 0.f : Xm.x, xbm = (k == 0) ? 0.f : Xm.y;
+                    const C dk = cconj(a.dtw[k]);
+                    C Va, Vb;
+                    Va.x = dk.x * Xk.x + dk.y * xam; Va.y = dk.y * Xk.x - dk.x * xam;
+                    Vb.x = dk.x * Xk.y + dk.y * xbm; Vb.y = dk.y * Xk.y - dk.x * xbm;
+                    C Zk; Zk.x = Va.x - Vb.y; Zk.y = Va.y + Vb.x;
+                    if (km != k) {
+                        const C dm = cconj(a.dtw[km]);
+                        C Wa, Wb;
+                        Wa.x = dm.x * Xm.x + dm.y * Xk.x; Wa.y = dm.y * Xm.x - dm.x * Xk.x;
+                        Wb.x = dm.x * Xm.y + dm.y * Xk.y; Wb.y = dm.y * Xm.y - dm.x * Xk.y;
+                        C Zm; Zm.x = Wa.x - Wb.y; Zm.y = Wa.y + Wb.x;
+                        z[padix(km)] = Zm;
+                    }
+                    z[padix(k)] = Zk;
+                }
+                __syncthreads();
+                fft_fixed_call<+1, LOGN>(z, t, a.ptw);
+            }
         }
         // ---- store: float4 per row (INV with an update reads its rows first) --------
         {
