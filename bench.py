@@ -477,17 +477,28 @@ def main():
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         elapsed = float(t.item())
     value = ws * args.steps / elapsed
-    # profiled region
-    torch.cuda.synchronize()
-    B.bfm_profile_begin(prof_steps * 40 + 64)
-    p0 = torch.cuda.Event(enable_timing=True)
-    p1 = torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    solver.iterate(prof_steps)
-    p1.record(stream)
-    torch.cuda.synchronize()
-    prof = B.bfm_profile_end()
-    prof_elapsed = p0.elapsed_time(p1) / 1e3
+    # profiled region: two passes of half the steps; per kernel kind the pass
+    # with the smaller time counts, so a transient slowdown of one pass (the
+    # GPU is shared) does not pick the dominant kernel
+    half = max(1, prof_steps // 2)
+    passes = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        B.bfm_profile_begin(half * 40 + 64)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        solver.iterate(half)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        passes.append((B.bfm_profile_end(), p0.elapsed_time(p1) / 1e3))
+    prof_steps = 2 * half
+    prof = {}
+    for k in passes[0][0]:
+        a, b = passes[0][0][k], passes[1][0].get(k, passes[0][0][k])
+        best = a if a[0] <= b[0] else b
+        prof[k] = (2 * best[0], 2 * best[1])
+    prof_elapsed = 2 * min(t for _, t in passes)
     res_timed = solver.finish(with_map=False)
 
     # ---- roofline of the dominant kernel (live CUDA-event times) ---------------------------
@@ -515,7 +526,8 @@ def main():
     breakdown["_profiled_region"] = {"steps": prof_steps,
                                      "ms_per_iter": prof_elapsed / prof_steps * 1e3,
                                      "note": "a second timed region with CUDA events around "
-                                             "every kernel group"}
+                                             "every kernel group (two passes of half the steps, "
+                                             "per kind the faster pass)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

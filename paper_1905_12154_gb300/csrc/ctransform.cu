@@ -1199,7 +1199,7 @@ int pick_K(int n)
     if (n <= 64) return 2;
     if (n <= 128) return 4;
     if (n <= 256) return 8;
-    if (n == 384) return 12;      // 32 chunks: no idle lane in the line's warp
+    if (n == 384) return 24;      // 16 chunks (a half warp per line, no idle lane)
     return 16;
 }
 
@@ -1242,6 +1242,8 @@ void* select_kernel(int K, bool contig, bool batched)
         case 4: return kernel_for<T, 4>(contig, batched);
         case 8: return kernel_for<T, 8>(contig, batched);
         case 12: return kernel_for<T, 12>(contig, batched);
+        case 24: return kernel_for<T, 24>(contig, batched);
+        case 32: return kernel_for<T, 32>(contig, batched);
         default: return kernel_for<T, 16>(contig, batched);
     }
 }
@@ -1368,9 +1370,9 @@ CtShape ct_default_shape(int kind, int n, int elem_bytes)
 
 static bool tile_K_ok(int n, int K)
 {
-    if (K != 1 && K != 2 && K != 4 && K != 8 && K != 12 && K != 16) return false;
+    if (K != 1 && K != 2 && K != 4 && K != 8 && K != 12 && K != 16 && K != 24 && K != 32) return false;
     if (K > n) return false;
-    if (K == 12 && n % 12 != 0) return false;
+    if ((K == 12 || K == 24) && n % K != 0) return false;
     return next_pow2((n + K - 1) / K) <= 512;
 }
 
@@ -1395,10 +1397,10 @@ static int max_lines(int kind, int n, int elem_bytes, int K)
 
 int ct_shape_candidates(int kind, int n, int elem_bytes, CtShape* out, int cap)
 {
-    static const int tileK[] = {1, 2, 4, 8, 12, 16};
+    static const int tileK[] = {1, 2, 4, 8, 12, 16, 24, 32};
     static const int rowK[] = {16, 32};
     const int* Ks = kind == CT_KIND_ROW ? rowK : tileK;
-    const int nK = kind == CT_KIND_ROW ? 2 : 6;
+    const int nK = kind == CT_KIND_ROW ? 2 : 8;
     int cnt = 0;
     for (int i = 0; i < nK; ++i) {
         const int K = Ks[i];

@@ -421,7 +421,7 @@ static bfm_status poisson_inverse(const Grid& g, const AxisTables* tabs, T* buf,
 
 // one CTA sums the FP64 partials of a half step's reductions (up to a few
 // thousand: one per CTA of the launch that produced them)
-constexpr int kFinThreads = 1024;
+constexpr int kFinThreads = 256;
 
 // The half step on 2-D grids with long columns (quadratic cost): phi is kept
 // in the grid's layout and psi in the transposed one, so the c-transforms

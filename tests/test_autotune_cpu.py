@@ -34,7 +34,7 @@ def test_candidates_are_valid_shapes(n, prec):
         assert len(set(cand)) == len(cand)
         assert B.bfm_tune_default(kind, n, prec) in cand
         for K, W in cand:
-            assert K <= n and K in ((16, 32) if kind == B.CT_KIND_ROW else (1, 2, 4, 8, 12, 16))
+            assert K <= n and K in ((16, 32) if kind == B.CT_KIND_ROW else (1, 2, 4, 8, 12, 16, 24, 32))
             G = _next_pow2(-(-n // K))
             assert G <= 512
             if kind == B.CT_KIND_ROW:
@@ -62,7 +62,7 @@ def test_set_get_clear():
 
 
 def test_set_rejects_non_candidates():
-    for bad in ((3, 0), (16, 3), (32, 0)):
+    for bad in ((3, 0), (16, 3), (24, 0), (64, 0)):
         with pytest.raises(B.BfmError) as e:
             B.bfm_tune_set(B.CT_KIND_TILE_COLS, 128, *bad)
         assert e.value.status == B.BFM_ERR_INVALID_ARG
