@@ -1363,9 +1363,11 @@ int ct_kind(const Grid& g, int axis)
 
 CtShape ct_default_shape(int kind, int n, int elem_bytes)
 {
-    (void)elem_bytes;
     if (kind == CT_KIND_ROW) return CtShape{row_cells_per_thread(n), 0};
-    return CtShape{pick_K(n), 0};
+    const CtShape s{pick_K(n), 0};
+    // 24 cells per thread where its lines fill whole warps, else 12
+    if (s.K == 24 && !ct_shape_valid(kind, n, elem_bytes, s)) return CtShape{12, 0};
+    return s;
 }
 
 static bool tile_K_ok(int n, int K)
@@ -1484,7 +1486,9 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes)
 
 CtPlan plan_ct_pass_default(const Grid& g, int axis, int elem_bytes)
 {
-    return plan_ct_tile(g, axis, elem_bytes, pick_K(g.n[axis]), 0);
+    const CtShape s = ct_default_shape(axis == 0 ? CT_KIND_TILE_ROWS : CT_KIND_TILE_COLS, g.n[axis],
+                                       elem_bytes);
+    return plan_ct_tile(g, axis, elem_bytes, s.K, s.W);
 }
 
 static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
