@@ -506,8 +506,8 @@ class BfmSolver:
 
 # --- launch shapes of the line c-transform (autotuner) -------------------------
 
-CT_KIND_TILE_ROWS, CT_KIND_TILE_COLS, CT_KIND_ROW = 0, 1, 2
-CT_KIND_NAMES = {0: "tile_rows", 1: "tile_cols", 2: "row"}
+CT_KIND_TILE_ROWS, CT_KIND_TILE_COLS, CT_KIND_ROW, CT_KIND_ROW_COLS = 0, 1, 2, 3
+CT_KIND_NAMES = {0: "tile_rows", 1: "tile_cols", 2: "row", 3: "row_cols"}
 
 
 def _prec_of_dtype(dtype) -> int:

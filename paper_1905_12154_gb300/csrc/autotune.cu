@@ -21,13 +21,14 @@
 namespace bfm {
 
 // The timing field: phi(x) = 0.45 (x - c)^2 + a sin(2 pi (4 x + 0.37 l)) along
-// line l, x the cell centre along the line.  The pass reads -phi, whose lifted
-// points hh j^2 - phi_j have curvature 0.1 plus the sine's, so each line is
-// convex on part of its length and loses points to the envelope elsewhere,
-// as the potentials of a solve do.
+// line l, x the cell centre along the line.  The pass works on -phi, whose
+// lifted points hh j^2 - phi_j have curvature 0.1 plus the sine's, so each
+// line is convex on part of its length and loses points to the envelope
+// elsewhere, as the potentials of a solve do.  As in a solve, an axis-0 pass
+// negates on load and passes along other axes do not: those get -phi stored.
 template <typename T>
 __global__ void tune_field_kernel(T* f, int n, long long nlines, int axis_stride_is_one,
-                                  long long n0)
+                                  long long n0, double sign)
 {
     const long long N = (long long)n * nlines;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
@@ -38,18 +39,18 @@ __global__ void tune_field_kernel(T* f, int n, long long nlines, int axis_stride
         const double x = (k + 0.5) / n;
         const double v = 0.45 * (x - 0.4) * (x - 0.4) +
                          1e-3 * sinpi(2.0 * (4.0 * x + 0.37 * (double)l));
-        f[i] = (T)v;
+        f[i] = (T)(sign * v);
     }
 }
 
 // The timing grid: lines of n cells along the kernel kind's axis, about 8 M
 // cells in all (at least two lines), split over a third axis where one axis
 // would exceed the longest supported line.
-static bool tune_grid(int kind, int n, Grid* g, int* axis)
+static bool tune_grid(int kind, int n, int elem_bytes, Grid* g, int* axis)
 {
     const long long L = std::max<long long>(2, (8LL << 20) / n);
     bfm_grid bg;
-    if (kind == CT_KIND_TILE_COLS) {
+    if (kind == CT_KIND_TILE_COLS || kind == CT_KIND_ROW_COLS) {
         const long long a = std::min<long long>(L, 2048), b = L / a;
         bg.n[0] = (int)a; bg.n[1] = n; bg.n[2] = (int)b;
         *axis = 1;
@@ -60,7 +61,7 @@ static bool tune_grid(int kind, int n, Grid* g, int* axis)
     }
     bg.ndim = bg.n[2] >= 2 ? 3 : 2;
     if (!make_grid(&bg, g)) return false;
-    return ct_kind(*g, *axis) == kind;
+    return ct_kind(*g, *axis, elem_bytes) == kind;
 }
 
 }  // namespace bfm
@@ -69,7 +70,7 @@ using namespace bfm;
 
 extern "C" int bfm_tune_candidates(int kind, int n, bfm_precision prec, int* K, int* W, int cap)
 {
-    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW || n < 2 || cap < 0) return -1;
+    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW_COLS || n < 2 || cap < 0) return -1;
     std::vector<CtShape> c(64);
     const int m = ct_shape_candidates(kind, n, prec == BFM_FP64 ? 8 : 4, c.data(), 64);
     for (int i = 0; i < m && i < cap; ++i) {
@@ -81,7 +82,7 @@ extern "C" int bfm_tune_candidates(int kind, int n, bfm_precision prec, int* K, 
 
 extern "C" int bfm_tune_default(int kind, int n, bfm_precision prec, int* K, int* W)
 {
-    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW || n < 2) return -1;
+    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW_COLS || n < 2) return -1;
     const CtShape s = ct_default_shape(kind, n, prec == BFM_FP64 ? 8 : 4);
     if (K) *K = s.K;
     if (W) *W = s.W;
@@ -91,7 +92,7 @@ extern "C" int bfm_tune_default(int kind, int n, bfm_precision prec, int* K, int
 extern "C" bfm_status bfm_tune_set(int kind, int n, bfm_precision prec, int K, int W)
 {
     const int eb = prec == BFM_FP64 ? 8 : 4;
-    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW || !ct_shape_valid(kind, n, eb, CtShape{K, W})) {
+    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW_COLS || !ct_shape_valid(kind, n, eb, CtShape{K, W})) {
         set_last_error("bfm_tune_set: not a candidate shape of this kernel kind and line length");
         return BFM_ERR_INVALID_ARG;
     }
@@ -129,10 +130,10 @@ extern "C" size_t bfm_autotune_scratch_bytes(int kind, int n, bfm_precision prec
 {
     Grid g;
     int axis = 0;
-    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW || n < 2 || !tune_grid(kind, n, &g, &axis))
+    const int eb = prec == BFM_FP64 ? 8 : 4;
+    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW_COLS || n < 2 || !tune_grid(kind, n, eb, &g, &axis))
         return 0;
-    const size_t eb = prec == BFM_FP64 ? 8 : 4;
-    return 2 * (size_t)g.N * eb + 256;
+    return 2 * (size_t)g.N * (size_t)eb + 256;
 }
 
 template <typename T>
@@ -141,7 +142,7 @@ static bfm_status autotune_impl(int kind, int n, void* scratch, size_t bytes, cu
 {
     Grid g;
     int axis = 0;
-    if (!tune_grid(kind, n, &g, &axis)) {
+    if (!tune_grid(kind, n, (int)sizeof(T), &g, &axis)) {
         set_last_error("bfm_autotune: this line length does not take this kernel kind");
         return BFM_ERR_INVALID_ARG;
     }
@@ -153,8 +154,12 @@ static bfm_status autotune_impl(int kind, int n, void* scratch, size_t bytes, cu
     }
     T* in = reinterpret_cast<T*>(scratch);
     T* out = in + g.N;
-    tune_field_kernel<T><<<num_sms() * 4, 256, 0, st>>>(in, n, g.N / n, axis == 0 ? 1 : 0, g.n[0]);
+    tune_field_kernel<T><<<num_sms() * 4, 256, 0, st>>>(in, n, g.N / n, axis == 0 ? 1 : 0, g.n[0],
+                                                         axis == 0 ? 1.0 : -1.0);
     BFM_LAUNCH_CHECK("tune_field_kernel");
+    // as in a solve: the first pass (axis 0) reads -phi, later passes the
+    // previous pass's output
+    const bool negate = axis == 0;
     std::vector<CtShape> cand(64);
     const int m = std::min(ct_shape_candidates(kind, n, eb, cand.data(), 64), 64);
     const CtShape def = ct_default_shape(kind, n, eb);
@@ -169,12 +174,12 @@ static bfm_status autotune_impl(int kind, int n, void* scratch, size_t bytes, cu
         if (cand[c].K == def.K && cand[c].W == def.W) def_idx = c;
         ct_set_tuned_shape(kind, n, eb, cand[c]);
         for (int r = 0; r < 2 && s == BFM_OK; ++r)
-            s = launch_ct_pass<T>(g, axis, in, out, true, nullptr, nullptr, nullptr, nullptr,
+            s = launch_ct_pass<T>(g, axis, in, out, negate, nullptr, nullptr, nullptr, nullptr,
                                   nullptr, 0, st, nullptr);
         double t[5];
         for (int r = 0; r < 5 && s == BFM_OK; ++r) {
             cudaEventRecord(ev[0], st);
-            s = launch_ct_pass<T>(g, axis, in, out, true, nullptr, nullptr, nullptr, nullptr,
+            s = launch_ct_pass<T>(g, axis, in, out, negate, nullptr, nullptr, nullptr, nullptr,
                                   nullptr, 0, st, nullptr);
             cudaEventRecord(ev[1], st);
             cudaError_t e = cudaEventSynchronize(ev[1]);
@@ -208,7 +213,7 @@ extern "C" bfm_status bfm_autotune(int kind, int n, bfm_precision prec, void* sc
                                    size_t scratch_bytes, void* stream, int* K_out, int* W_out,
                                    double* ms_out, int ms_cap)
 {
-    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW || n < 2) {
+    if (kind < CT_KIND_TILE_ROWS || kind > CT_KIND_ROW_COLS || n < 2) {
         set_last_error("bfm_autotune: unknown kernel kind or line length below 2");
         return BFM_ERR_INVALID_ARG;
     }
@@ -232,11 +237,11 @@ extern "C" int bfm_tune_passes(const bfm_grid* grid, bfm_precision prec, int bat
     };
     if (!batched && g.ndim == 2 && transposed_axis1(g, eb)) {
         // long columns: both axes are swept as rows (of the grid or of its transposed copy)
-        add(ct_kind(g, 0), g.n[0]);
+        add(ct_kind(g, 0, eb), g.n[0]);
         const Grid gt = transposed_grid(g);
-        add(ct_kind(gt, 0), gt.n[0]);
+        add(ct_kind(gt, 0, eb), gt.n[0]);
     } else {
-        for (int a = 0; a < g.ndim; ++a) add(ct_kind(g, a), g.n[a]);
+        for (int a = 0; a < g.ndim; ++a) add(ct_kind(g, a, eb), g.n[a]);
     }
     for (int i = 0; i < m && i < cap; ++i) {
         if (kinds) kinds[i] = kk[i];

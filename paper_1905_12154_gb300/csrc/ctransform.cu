@@ -61,6 +61,7 @@ struct CtArgs {
     int vec4;             // rows may be moved as float4 (n % 4 == 0, 16-byte aligned)
     int lw;               // log2(W); interleaved tiles have W a power of two
     int ioff;             // row kernel: byte offset of the int scratch in shared memory
+    int soff;             // row kernel on interleaved tiles: byte offset of the output tile
 };
 
 // Shared-memory layout of a line: thread t owns cells [tK, tK+K).  Stored
@@ -749,12 +750,37 @@ __device__ void merge_pair_t(const T* f, const short* stk, short* beg, short* en
 //   * the outputs go from registers straight to global memory, four at a
 //     time (a thread's 32 outputs are one 128-byte line), fused with the dual
 //     dot product.
+// COLS: the same phases on lines along an axis > 0 (columns of 2-D grids,
+// axes 1 and 2 of 3-D grids), W neighbouring lines per CTA as one
+// interleaved tile: the CTA loads the tile cooperatively (each element
+// position is W consecutive words of global memory), each group builds its
+// line's envelope as above and writes its outputs into a shared copy of the
+// tile, and the CTA stores the tile cooperatively, fused with the dual dot.
+// Two CTA barriers per tile replace the per-row independence of the rows.
+// The value arrays are double-buffered: while the groups work on one tile,
+// the next tile is on its way into the other buffer (cp.async), so the CTA
+// does not sit out the load latency of every tile (passes that negate or
+// take a dot on load copy synchronously).
 // ---------------------------------------------------------------------------
 constexpr int kRowMinN = 256;          // rows longer than this take the row kernel
 constexpr int kRowLongN = 1024;        // from here 32 cells per thread, else 16
 
 
 static int row_cells_per_thread(int n) { return n >= kRowLongN ? 32 : 16; }
+
+// Asynchronous global -> shared copies of one element (cp.async, 4 or 8
+// bytes, cached in L1), grouped and waited for by the issuing thread.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" :: "r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" :: "r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Barrier of one line group (G >= 32 threads, whole warps): a single warp
 // uses the warp barrier, larger groups named barrier 1 + w.
@@ -798,7 +824,7 @@ __device__ __forceinline__ bool fix_round_row(const T* f, const short* stk, shor
 }
 
 // BATCHED: blockIdx.y selects the problem, whose arguments come from `batch`.
-template <typename T, int K, bool BATCHED>
+template <typename T, int K, bool BATCHED, bool COLS>
 __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtArgs<T>* batch)
 {
     const CtArgs<T>& a = BATCHED ? batch[blockIdx.y] : a0;
@@ -827,6 +853,8 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
     const int lane = tid & 31;
     T* f = fs + (size_t)w * a.LD;
     short* stk = stk_all + (size_t)w * a.LDI;
+    // COLS: the second value buffer follows the output tile
+    T* fs_next = reinterpret_cast<T*>(smem_raw + a.soff) + (size_t)W * a.LD;
     short* beg = seg_all + (size_t)w * 3 * G;
     short* end = beg + G;
     short* nzs = end + G;
@@ -841,9 +869,67 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
     Acc<T> acc_t_in, acc_t_out;
     double acc_in = 0.0, acc_out = 0.0;
     const long long groups = (long long)gridDim.x * W;
+    // COLS: the output tile in shared memory, laid out like the value arrays
+    T* stg_all = reinterpret_cast<T*>(smem_raw + a.soff);
+    const long long nitems = COLS ? a.lt.ntiles : nrows;
+    const long long item0 = COLS ? (long long)blockIdx.x : (long long)blockIdx.x * W + w;
+    const long long istep = COLS ? (long long)gridDim.x : groups;
+    const bool prefetch = COLS && !a.negate && !a.w_in;
+    // copies of tile `it` into the value buffers at `dst` (one element per
+    // position and line, position-major like the global layout)
+    auto issue_tile = [&](long long it, T* dst) {
+        const Tile tn = tile_at(a.lt, it);
+        const int lw = a.lw, total = n << lw, nth = (int)blockDim.x;
+        for (int e = tid; e < total; e += nth) {
+            const int ww = e & (W - 1), pp = e >> lw;
+            if (ww < tn.wact)
+                cp_async_elem(dst + (size_t)ww * a.LD + SK::f(pp),
+                              a.in + tn.base0 + ww + (long long)pp * a.lt.es);
+        }
+        cp_async_commit();
+    };
+    if (COLS && prefetch && item0 < nitems) issue_tile(item0, fs);
 
-    for (long long row = (long long)blockIdx.x * W + w; row < nrows; row += groups) {
-        const long long rb = row * n;
+    for (long long item = item0; item < nitems; item += istep) {
+        const long long rb = COLS ? 0 : item * n;
+        Tile tl;
+        bool active = true;
+        if constexpr (COLS) {
+            // ---- load: the CTA reads the tile, position-major (W consecutive
+            // words per position), kU elements in flight per thread ----------
+            tl = tile_at(a.lt, item);
+            active = w < tl.wact;
+            f = fs + (size_t)w * a.LD;
+            if (prefetch) {
+                cp_async_wait_all();
+                __syncthreads();
+                // the other buffer held the tile before this one, whose
+                // groups all passed the barrier before its store
+                if (item + istep < nitems) issue_tile(item + istep, fs_next);
+            } else {
+            const int lw = a.lw, total = n << lw, nth = (int)blockDim.x;
+            for (int e0 = tid; e0 < total; e0 += kU * nth) {
+                T v[kU], u[kU];
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int e = e0 + k * nth, ww = e & (W - 1), pp = e >> lw;
+                    const bool ok = e < total && ww < tl.wact;
+                    const long long ad = tl.base0 + ww + (long long)pp * a.lt.es;
+                    v[k] = ok ? a.in[ad] : (T)0;
+                    u[k] = (ok && a.w_in) ? a.w_in[ad] : (T)0;
+                }
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int e = e0 + k * nth, ww = e & (W - 1), pp = e >> lw;
+                    if (e < total && ww < tl.wact) {
+                        if (a.w_in) acc_t_in.add_prod(v[k], u[k]);
+                        fs[(size_t)ww * a.LD + SK::f(pp)] = a.negate ? -v[k] : v[k];
+                    }
+                }
+            }
+            __syncthreads();
+            }
+        } else {
         // ---- load: the group reads its row with coalesced loads, kU at a time ----
         if (sizeof(T) == 4 && a.vec4) {
             const float4* src = reinterpret_cast<const float4*>(a.in + rb);
@@ -893,6 +979,8 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
             }
         }
         group_sync(w, G);
+        }
+        if (active) {
         // ---- A: envelope of this thread's chunk (stack in place) -------------
         // A chunk of K = 2^lg cells lies inside one skew block, so its cells
         // are consecutive from fl / sl.
@@ -964,11 +1052,16 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
         }
         group_sync(w, G);
         // stores four outputs of this thread (float4 where the row allows) and
-        // adds them to the dual dot
+        // adds them to the dual dot; COLS: into the shared output tile
         T* dst = a.out + rb;
         const T* wo = a.w_out ? a.w_out + rb : nullptr;
+        T* stg = stg_all + (size_t)w * a.LD;
         auto store4 = [&](int x0, const T* o) {
-            if (sizeof(T) == 4 && a.vec4 && x0 + 4 <= hi) {
+            if constexpr (COLS) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (x0 + k < hi) stg[SK::f(x0 + k)] = o[k];
+            } else if (sizeof(T) == 4 && a.vec4 && x0 + 4 <= hi) {
                 float4 v4 = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
                 *reinterpret_cast<float4*>(dst + x0) = v4;
                 if (wo) {
@@ -1174,9 +1267,26 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
             }
         }
         }
+        }
+        if constexpr (COLS) {
+            // ---- store: the CTA writes the tile back, position-major, with
+            // the dual dot; the next tile's load writes only the value arrays
+            __syncthreads();
+            const int lw = a.lw, total = n << lw, nth = (int)blockDim.x;
+            for (int e = tid; e < total; e += nth) {
+                const int ww = e & (W - 1), pp = e >> lw;
+                if (ww < tl.wact) {
+                    const T o = stg_all[(size_t)ww * a.LD + SK::f(pp)];
+                    const long long ad = tl.base0 + ww + (long long)pp * a.lt.es;
+                    a.out[ad] = o;
+                    if (a.w_out) acc_t_out.add_prod(o, a.w_out[ad]);
+                }
+            }
+        }
         acc_in += acc_t_in.take();
         acc_out += acc_t_out.take();
-        group_sync(w, G);            // the next row overwrites this group's arrays
+        if constexpr (!COLS) group_sync(w, G);   // the next row overwrites this group's arrays
+        if (prefetch) { T* tb = fs; fs = fs_next; fs_next = tb; }
     }
     if (a.part_in) {
         const double s = block_sum(acc_in, red);
@@ -1307,15 +1417,18 @@ static CtPlan plan_ct_tile(const Grid& g, int axis, int elem_bytes, int K, int W
     return p;
 }
 
-static bool use_row_kernel(const Grid& g, int axis) { return axis == 0 && g.n[0] > kRowMinN; }
-
 // Row kernel plan: K = 32 or 16 cells per thread, G = the next power of two
 // of n / K (at least 32 for n > 256, so every group is whole warps), as many
 // groups per CTA as fit 512 threads and about 110 KB (two CTAs per SM).
-static CtPlan plan_ct_row_shape(const Grid& g, int elem_bytes, int K, int Wreq)
+// Lines along axis > 0 (COLS) come as interleaved tiles of W neighbouring
+// lines, W a power of two, with a second value-sized array per line for the
+// output tile and a leading dimension chosen against bank conflicts of the
+// position-major tile loads and stores.
+static CtPlan plan_ct_row_shape(const Grid& g, int elem_bytes, int K, int Wreq, int axis = 0)
 {
     CtPlan p;
-    const int n = g.n[0];
+    const int n = g.n[axis];
+    const bool cols = axis > 0;
     p.K = K;
     p.G = next_pow2((n + p.K - 1) / p.K);
     const int chunks = (n + p.K - 1) / p.K + 1;
@@ -1327,21 +1440,49 @@ static CtPlan plan_ct_row_shape(const Grid& g, int elem_bytes, int K, int Wreq)
     // int scratch per group: 2 nwl scan words and 2 counts; FP32 rows add the
     // cell mask of owner starts (one bit per cell) and G writer masks
     const size_t ints = 2 * (size_t)nwl + 2 + (elem_bytes == 4 ? (size_t)((n + 31) >> 5) + p.G : 0);
-    const size_t line_bytes = (size_t)p.LD * elem_bytes + (size_t)p.LDI * 2 + 3 * (size_t)p.G * 2 +
-                              4 * ints;
+    // COLS: value arrays twice (double-buffered loads) and the output tile
+    const size_t line_bytes = (size_t)p.LD * elem_bytes * (cols ? 3 : 1) + (size_t)p.LDI * 2 +
+                              3 * (size_t)p.G * 2 + 4 * ints;
+    // (COLS: with room for the leading dimension's padding below)
+    const size_t budget_line = line_bytes + (cols ? 3 * 32 * (size_t)elem_bytes : 0);
     int W = 512 / p.G;
     if (W < 1) W = 1;
-    while (W > 1 && (size_t)W * line_bytes > 110 * 1024) --W;
+    while (W > 1 && (size_t)W * budget_line > 110 * 1024) --W;
     if (Wreq > 0 && W > Wreq) W = Wreq;
+    if (cols) {
+        int p2 = 1;
+        while (p2 * 2 <= W) p2 *= 2;
+        W = p2;
+        int best = 1 << 30, LD = p.LD;
+        for (int cand = p.LD; cand <= p.LD + 32; cand += 2) {
+            const int c = bank_conflicts(cand, W, elem_bytes / 4);
+            if (c < best) { best = c; LD = cand; }
+        }
+        p.LD = LD;
+    }
     p.W = W;
     size_t off = (size_t)W * p.LD * elem_bytes + (size_t)W * p.LDI * 2 + (size_t)W * 3 * p.G * 2;
     off = (off + 15) & ~(size_t)15;
     p.ioff = (int)off;
     p.LDH = 0;
-    p.smem = off + (size_t)W * ints * 4 + 16;
+    size_t end = off + (size_t)W * ints * 4;
+    end = (end + 15) & ~(size_t)15;
+    p.soff = (int)end;
+    p.smem = end + (cols ? 2 * (size_t)W * p.LD * elem_bytes : 0) + 16;
     p.threads = W * p.G;
-    p.tiles = make_tiles(g, 0, W);
+    p.tiles = make_tiles(g, axis, W);
     return p;
+}
+
+// Lines of more than 256 cells take the row kernel: rows always, lines along
+// the other axes when a tile of the default shape spans at least 32 bytes per
+// element position (one DRAM sector), else the tile kernel.
+static bool use_row_kernel(const Grid& g, int axis, int elem_bytes)
+{
+    const int n = g.n[axis];
+    if (n <= kRowMinN) return false;
+    if (axis == 0) return true;
+    return plan_ct_row_shape(g, elem_bytes, row_cells_per_thread(n), 0, axis).W * elem_bytes >= 32;
 }
 
 // ---------------------------------------------------------------------------
@@ -1355,15 +1496,17 @@ static CtPlan plan_ct_row_shape(const Grid& g, int elem_bytes, int K, int Wreq)
 // the fastest here, and every later plan of that kind and length takes it.
 // Any candidate gives the same envelope (the same exact-discrete transform),
 // so a tuned shape changes timing, not results beyond rounding order.
-int ct_kind(const Grid& g, int axis)
+int ct_kind(const Grid& g, int axis, int elem_bytes)
 {
-    if (use_row_kernel(g, axis)) return CT_KIND_ROW;
+    if (use_row_kernel(g, axis, elem_bytes)) return axis == 0 ? CT_KIND_ROW : CT_KIND_ROW_COLS;
     return axis == 0 ? CT_KIND_TILE_ROWS : CT_KIND_TILE_COLS;
 }
 
+static bool row_kind(int kind) { return kind == CT_KIND_ROW || kind == CT_KIND_ROW_COLS; }
+
 CtShape ct_default_shape(int kind, int n, int elem_bytes)
 {
-    if (kind == CT_KIND_ROW) return CtShape{row_cells_per_thread(n), 0};
+    if (row_kind(kind)) return CtShape{row_cells_per_thread(n), 0};
     const CtShape s{pick_K(n), 0};
     // 24 cells per thread where its lines fill whole warps, else 12
     if (s.K == 24 && !ct_shape_valid(kind, n, elem_bytes, s)) return CtShape{12, 0};
@@ -1389,11 +1532,12 @@ static bool row_K_ok(int n, int K)
 static int max_lines(int kind, int n, int elem_bytes, int K)
 {
     int dims[3] = {n, 64, 1};
-    if (kind == CT_KIND_TILE_COLS) { dims[0] = 64; dims[1] = n; }
+    const bool cols = kind == CT_KIND_TILE_COLS || kind == CT_KIND_ROW_COLS;
+    if (cols) { dims[0] = 64; dims[1] = n; }
     bfm_grid bg{2, {dims[0], dims[1], 1}};
     Grid g;
     make_grid(&bg, &g);
-    if (kind == CT_KIND_ROW) return plan_ct_row_shape(g, elem_bytes, K, 0).W;
+    if (row_kind(kind)) return plan_ct_row_shape(g, elem_bytes, K, 0, cols ? 1 : 0).W;
     return plan_ct_tile(g, kind == CT_KIND_TILE_COLS ? 1 : 0, elem_bytes, K, 0).W;
 }
 
@@ -1401,12 +1545,12 @@ int ct_shape_candidates(int kind, int n, int elem_bytes, CtShape* out, int cap)
 {
     static const int tileK[] = {1, 2, 4, 8, 12, 16, 24, 32};
     static const int rowK[] = {16, 32};
-    const int* Ks = kind == CT_KIND_ROW ? rowK : tileK;
-    const int nK = kind == CT_KIND_ROW ? 2 : 8;
+    const int* Ks = row_kind(kind) ? rowK : tileK;
+    const int nK = row_kind(kind) ? 2 : 8;
     int cnt = 0;
     for (int i = 0; i < nK; ++i) {
         const int K = Ks[i];
-        if (kind == CT_KIND_ROW ? !row_K_ok(n, K) : !tile_K_ok(n, K)) continue;
+        if (row_kind(kind) ? !row_K_ok(n, K) : !tile_K_ok(n, K)) continue;
         const int Wm = max_lines(kind, n, elem_bytes, K);
         const int G = next_pow2((n + K - 1) / K);
         // the unrestricted W and up to two halvings of it, keeping CTAs of
@@ -1491,10 +1635,22 @@ CtPlan plan_ct_pass_default(const Grid& g, int axis, int elem_bytes)
     return plan_ct_tile(g, axis, elem_bytes, s.K, s.W);
 }
 
-static CtPlan plan_ct_row(const Grid& g, int elem_bytes)
+static CtPlan plan_ct_row(const Grid& g, int axis, int elem_bytes)
 {
-    const CtShape s = shape_for(CT_KIND_ROW, g.n[0], elem_bytes);
-    return plan_ct_row_shape(g, elem_bytes, s.K, s.W);
+    const CtShape s = shape_for(axis == 0 ? CT_KIND_ROW : CT_KIND_ROW_COLS, g.n[axis], elem_bytes);
+    return plan_ct_row_shape(g, elem_bytes, s.K, s.W, axis);
+}
+
+// the row kernel for K cells per thread, batched or not, rows or interleaved tiles
+template <typename T>
+static void* row_kernel_for(int K, bool batched, bool cols)
+{
+    if (cols) {
+        if (batched) return K == 32 ? (void*)ct_row_kernel<T, 32, true, true> : (void*)ct_row_kernel<T, 16, true, true>;
+        return K == 32 ? (void*)ct_row_kernel<T, 32, false, true> : (void*)ct_row_kernel<T, 16, false, true>;
+    }
+    if (batched) return K == 32 ? (void*)ct_row_kernel<T, 32, true, false> : (void*)ct_row_kernel<T, 16, true, false>;
+    return K == 32 ? (void*)ct_row_kernel<T, 32, false, false> : (void*)ct_row_kernel<T, 16, false, false>;
 }
 
 template <typename T>
@@ -1514,6 +1670,7 @@ static CtArgs<T> make_ct_args(const Grid& g, int axis, const CtPlan& p, const T*
     a.lw = 0;
     while ((1 << a.lw) < p.W) ++a.lw;
     a.ioff = p.ioff;
+    a.soff = p.soff;
     return a;
 }
 
@@ -1529,10 +1686,16 @@ static int ct_blocks(const CtPlan& p, int max_blocks)
 
 int ct_pass_blocks(const Grid& g, int axis, int elem_bytes, int max_blocks)
 {
-    if (use_row_kernel(g, axis)) {
-        const CtPlan p = plan_ct_row(g, elem_bytes);
-        long long blocks = (p.tiles.nlines + p.W - 1) / p.W;
-        const long long cap = (long long)num_sms() * 2;      // two resident CTAs per SM
+    if (use_row_kernel(g, axis, elem_bytes)) {
+        const CtPlan p = plan_ct_row(g, axis, elem_bytes);
+        long long blocks = p.tiles.ntiles;
+        // one resident wave: 1024 threads per SM at 64 registers each
+        // (launch bounds 512, 2), fewer where shared memory runs out
+        int per_sm = 1024 / p.threads;
+        const int by_smem = (int)((227 * 1024) / (p.smem + 1024));
+        if (per_sm > by_smem) per_sm = by_smem;
+        if (per_sm < 1) per_sm = 1;
+        const long long cap = (long long)num_sms() * per_sm;
         if (blocks > cap) blocks = cap;
         if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
         if (blocks < 1) blocks = 1;
@@ -1546,11 +1709,11 @@ bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool neg
                           const T* w_in, double* part_in, const T* w_out, double* part_out,
                           const int* done, int max_blocks, cudaStream_t st, int* blocks_used)
 {
-    if (use_row_kernel(g, axis)) {
-        CtPlan p = plan_ct_row(g, (int)sizeof(T));
+    if (use_row_kernel(g, axis, (int)sizeof(T))) {
+        CtPlan p = plan_ct_row(g, axis, (int)sizeof(T));
         CtArgs<T> a = make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out,
                                       done);
-        void* k = (p.K == 32) ? (void*)ct_row_kernel<T, 32, false> : (void*)ct_row_kernel<T, 16, false>;
+        void* k = row_kernel_for<T>(p.K, false, axis > 0);
         BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
         const int blocks = ct_pass_blocks(g, axis, (int)sizeof(T), max_blocks);
         const CtArgs<T>* none = nullptr;
@@ -1584,7 +1747,8 @@ void fill_ct_batch_args(const Grid& g, int axis, const T* in, T* out, bool negat
                         double* part_in, const T* w_out, double* part_out, const int* done,
                         void* host_slot)
 {
-    CtPlan p = use_row_kernel(g, axis) ? plan_ct_row(g, (int)sizeof(T)) : plan_ct_pass(g, axis, (int)sizeof(T));
+    CtPlan p = use_row_kernel(g, axis, (int)sizeof(T)) ? plan_ct_row(g, axis, (int)sizeof(T))
+                                                       : plan_ct_pass(g, axis, (int)sizeof(T));
     *reinterpret_cast<CtArgs<T>*>(host_slot) =
         make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out, done);
 }
@@ -1595,10 +1759,10 @@ template <typename T>
 bfm_status launch_ct_pass_batched(const Grid& g, int axis, int nprob, const void* dev_args,
                                   cudaStream_t st)
 {
-    if (use_row_kernel(g, axis)) {
-        // long rows: the row kernel, one grid row per problem
-        const CtPlan p = plan_ct_row(g, (int)sizeof(T));
-        void* k = (p.K == 32) ? (void*)ct_row_kernel<T, 32, true> : (void*)ct_row_kernel<T, 16, true>;
+    if (use_row_kernel(g, axis, (int)sizeof(T))) {
+        // long lines: the row kernel (rows or interleaved tiles), per problem
+        const CtPlan p = plan_ct_row(g, axis, (int)sizeof(T));
+        void* k = row_kernel_for<T>(p.K, true, axis > 0);
         BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
         const int blocks = ct_pass_blocks(g, axis, (int)sizeof(T), kMaxPartials);
         CtArgs<T> dummy;

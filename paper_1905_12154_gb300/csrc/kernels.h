@@ -8,6 +8,7 @@ namespace bfm {
 struct CtPlan {
     int K, G, W, LD, LDI, LDH, threads;
     int ioff = 0;             // row kernel: byte offset of the int scratch
+    int soff = 0;             // row kernel on interleaved tiles: byte offset of the output tile
     size_t smem;
     LineTiles tiles;
 };
@@ -37,9 +38,9 @@ struct DctPlan {
 
 // c-transform launch shapes: K cells per thread, W lines per CTA (0: as many
 // as the thread and shared-memory limits allow), per kernel kind
-enum { CT_KIND_TILE_ROWS = 0, CT_KIND_TILE_COLS = 1, CT_KIND_ROW = 2 };
+enum { CT_KIND_TILE_ROWS = 0, CT_KIND_TILE_COLS = 1, CT_KIND_ROW = 2, CT_KIND_ROW_COLS = 3 };
 struct CtShape { int K, W; };
-int ct_kind(const Grid& g, int axis);
+int ct_kind(const Grid& g, int axis, int elem_bytes);
 CtShape ct_default_shape(int kind, int n, int elem_bytes);
 int ct_shape_candidates(int kind, int n, int elem_bytes, CtShape* out, int cap);
 bool ct_shape_valid(int kind, int n, int elem_bytes, CtShape s);

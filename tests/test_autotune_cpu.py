@@ -6,7 +6,8 @@ import pytest
 
 from paper_1905_12154_gb300 import binding as B
 
-KINDS = (B.CT_KIND_TILE_ROWS, B.CT_KIND_TILE_COLS, B.CT_KIND_ROW)
+KINDS = (B.CT_KIND_TILE_ROWS, B.CT_KIND_TILE_COLS, B.CT_KIND_ROW, B.CT_KIND_ROW_COLS)
+ROW_KINDS = (B.CT_KIND_ROW, B.CT_KIND_ROW_COLS)
 
 
 def _next_pow2(x):
@@ -28,20 +29,20 @@ def clean_table():
 def test_candidates_are_valid_shapes(n, prec):
     for kind in KINDS:
         cand = B.bfm_tune_candidates(kind, n, prec)
-        if kind == B.CT_KIND_ROW and n <= 256:
-            assert cand == []                  # short rows never take the row kernel
+        if kind in ROW_KINDS and n <= 256:
+            assert cand == []                  # short lines never take the row kernel
             continue
         assert len(set(cand)) == len(cand)
         assert B.bfm_tune_default(kind, n, prec) in cand
         for K, W in cand:
-            assert K <= n and K in ((16, 32) if kind == B.CT_KIND_ROW else (1, 2, 4, 8, 12, 16, 24, 32))
+            assert K <= n and K in ((16, 32) if kind in ROW_KINDS else (1, 2, 4, 8, 12, 16, 24, 32))
             G = _next_pow2(-(-n // K))
             assert G <= 512
-            if kind == B.CT_KIND_ROW:
+            if kind in ROW_KINDS:
                 assert G >= 32                 # row groups are whole warps
             if W:
                 assert W * G <= 512 and W * G >= 32
-                if kind == B.CT_KIND_TILE_COLS:
+                if kind in (B.CT_KIND_TILE_COLS, B.CT_KIND_ROW_COLS):
                     assert W & (W - 1) == 0    # interleaved tiles: a power of two
                 if G < 32:
                     assert (W * G) % 32 == 0
@@ -82,9 +83,16 @@ def test_pick_keeps_default_within_margin():
 
 def test_passes_of_a_solve():
     R, C, T = B.CT_KIND_ROW, B.CT_KIND_TILE_COLS, B.CT_KIND_TILE_ROWS
+    RC = B.CT_KIND_ROW_COLS
     assert B.bfm_tune_passes((4096, 4096)) == [(R, 4096)]   # long columns: rows of a transposed copy
-    assert B.bfm_tune_passes((512, 512)) == [(R, 512), (C, 512)]
+    # columns of more than 256 cells: the row kernel on interleaved tiles
+    assert B.bfm_tune_passes((512, 512)) == [(R, 512), (RC, 512)]
     assert B.bfm_tune_passes((64, 128)) == [(T, 128), (C, 64)]
-    assert B.bfm_tune_passes((384, 384, 384)) == [(R, 384), (C, 384)]
+    assert B.bfm_tune_passes((384, 384, 384)) == [(R, 384), (RC, 384)]
+    assert B.bfm_tune_passes((300, 5, 3)) == [(T, 3), (C, 5), (RC, 300)]
+    # row-kernel tiles of 1024-cell columns would hold fewer than 32 bytes per
+    # position: the tile kernel, or (FP64) rows of a transposed copy
+    assert B.bfm_tune_passes((1024, 3)) == [(T, 3), (C, 1024)]
+    assert B.bfm_tune_passes((1024, 3), B.BFM_FP64) == [(T, 3), (R, 1024)]
     assert B.bfm_tune_passes((2048, 512)) == [(R, 512), (R, 2048)]
     assert B.bfm_tune_passes((2048, 512), batched=True) == [(R, 512), (C, 2048)]

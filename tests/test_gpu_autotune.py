@@ -34,11 +34,12 @@ def clean_table(B):
 
 def _shape(kind, n, lines=37):
     # the grid whose passes take (kind, n): rows of n cells, or columns of n
-    return (n, lines) if kind == 1 else (lines, n)
+    return (n, lines) if kind in (1, 3) else (lines, n)
 
 
 CASES = [(0, 64), (0, 100), (0, 128), (0, 256), (1, 64), (1, 128), (1, 200), (1, 256),
-         (1, 384), (1, 512), (2, 384), (2, 512), (2, 1000), (2, 1024), (2, 4096)]
+         (1, 1024), (2, 384), (2, 512), (2, 1000), (2, 1024), (2, 4096), (3, 300), (3, 384),
+         (3, 512)]
 
 
 @pytest.mark.parametrize("kind,n", CASES, ids=lambda v: str(v))
@@ -62,7 +63,7 @@ def test_every_candidate_shape_matches_oracle(B, kind, n, dt):
         assert err <= tol, (kind, n, K, W, err)
 
 
-@pytest.mark.parametrize("kind,n", [(1, 128), (2, 512), (2, 4096)], ids=str)
+@pytest.mark.parametrize("kind,n", [(1, 128), (2, 512), (2, 4096), (3, 384)], ids=str)
 def test_autotune_picks_a_candidate_and_stores_it(B, kind, n):
     r = B.bfm_autotune(kind, n, B.BFM_FP32)
     cand = B.bfm_tune_candidates(kind, n, B.BFM_FP32)

@@ -42,11 +42,14 @@ def host(t):
 
 # rows of more than 256 cells take the row kernel (one thread group per row,
 # 16 cells per thread below 1024, else 32): aligned, ragged (257, 300, 1500)
-# and unaligned (511, 1027) lengths, in 2-D and 3-D; lines of 384 cells along
-# axes 1 and 2 take tiles of 12 cells per thread
+# and unaligned (511, 1027) lengths, in 2-D and 3-D; lines of more than 256
+# cells along axes 1 and 2 take the same kernel on interleaved tiles of 16
+# lines (257-, 300- and 384-cell columns), with the last tile of a plane
+# partly filled where the axis-0 length is not a multiple of 16 (3, 8, 40,
+# 20); shorter lines and 1024-cell columns take tiles of the tile kernel
 CT_SHAPES = [(2, 2), (7, 5), (64, 64), (33, 100), (257, 96), (48, 31, 20), (9, 40, 13),
              (300, 5, 3), (511, 7), (1024, 3), (1500, 4), (1027, 3), (4096, 2),
-             (6, 384, 32), (384, 4, 8), (3, 384)]
+             (6, 384, 32), (384, 4, 8), (3, 384), (3, 300, 40), (260, 3, 20)]
 
 
 @pytest.mark.parametrize("shape", CT_SHAPES, ids=str)
@@ -72,7 +75,8 @@ def test_ctransform_fp32(B, shape):
 # |x|^2/2 - phi affine along every line: the rounded FP32 values leave many
 # parabolas on the envelope that meet at nearly one point, where the FP32
 # owner ranking can see start cells decrease and hands the line to the sweep;
-# rows of 4096 and 1500 (row kernel), 300-cell columns and short rows (tiles)
+# rows of 4096 and 1500 (row kernel), 300- and 384-cell columns (row kernel
+# on interleaved tiles) and short rows (tiles)
 DEGENERATE_SHAPES = [(4096, 3), (6, 1500), (300, 64), (40, 200), (5, 384, 9)]
 
 
