@@ -924,8 +924,8 @@ dct_row_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
                 const float wk = (kk == 0) ? 1.f : 2.f;
                 const float la = La + lk, lb = Lb + lk;
                 float ga = 0.f, gb = 0.f;
-                if (la > 0.f) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
-                if (hb && lb > 0.f) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
+                if (la > 0.f) { ga = __fdividef(v.x, la); gsum.add_prod(wa * wk * v.x, ga); }
+                if (hb && lb > 0.f) { gb = __fdividef(v.y, lb); gsum.add_prod(wb * wk * v.y, gb); }
                 v.x = ga; v.y = gb;
                 return v;
             };
@@ -967,9 +967,9 @@ dct_row_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
             __syncthreads();
             fft_fixed_call<+1, LOGN>(z, t, a.ptw);
         } else {
+        // FWD: forward FFT and the DCT-II split; INV: inverse twiddle and FFT
         if (MODE != DCT_INV) {
-                if (MODE == DCT_MID) fft_fixed_call<-1, LOGN>(z, t, a.ptw);
-                else fft_fixed<-1, LOGN>(z, t, a.ptw);
+                fft_fixed<-1, LOGN>(z, t, a.ptw);
                 // DCT-II from the FFT of the pair (Makhoul): split the two real
                 // lines' spectra, then twiddle by e^{-i pi k/(2n)}
                 for (int k = t; k <= n / 2; k += T) {
@@ -990,26 +990,6 @@ dct_row_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
                     }
                     z[padix(k)] = outk;
                 }
-                __syncthreads();
-            }
-            if (MODE == DCT_MID) {
-                // divide by the eigenvalue lambda(row) + lambda(k) (zero mode -> 0)
-                // and accumulate G = sum w |f^|^2 / lambda (Parseval weights 1, 2)
-                const long long ia = ra, ib = ra + 1;
-                const float La = a.lam_a0[ia], Lb = hb ? a.lam_a0[ib] : 0.f;
-                const float wa = (ia == 0) ? 1.f : 2.f, wb = 2.f;
-                for (int k = t; k < n; k += T) {
-                    const float lk = a.lam_axis[k];
-                    const float wk = (k == 0) ? 1.f : 2.f;
-                    C v = z[padix(k)];
-                    const float la = La + lk, lb = Lb + lk;
-                    float ga = 0.f, gb = 0.f;
-                    if (la > 0.f) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
-                    if (hb && lb > 0.f) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
-                    v.x = ga; v.y = gb;
-                    z[padix(k)] = v;
-                }
-                acc += gsum.take();
                 __syncthreads();
             }
             if (MODE != DCT_FWD) {
@@ -1263,8 +1243,8 @@ __global__ void __launch_bounds__(512, 2) dct384_kernel(DctArgs<float> a)
                 C v = z[padix(k)];
                 const float la = La + lk, lb = Lb + lk;
                 float ga = 0.f, gb = 0.f;
-                if (la > 0.f) { ga = v.x / la; gsum.add_prod(wa * wk * v.x, ga); }
-                if (lb > 0.f) { gb = v.y / lb; gsum.add_prod(wb * wk * v.y, gb); }
+                if (la > 0.f) { ga = __fdividef(v.x, la); gsum.add_prod(wa * wk * v.x, ga); }
+                if (lb > 0.f) { gb = __fdividef(v.y, lb); gsum.add_prod(wb * wk * v.y, gb); }
                 v.x = ga; v.y = gb;
                 z[padix(k)] = v;
             }
