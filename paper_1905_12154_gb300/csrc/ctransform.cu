@@ -37,6 +37,8 @@
 #include <map>
 #include <mutex>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -935,30 +937,37 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
             const float4* src = reinterpret_cast<const float4*>(a.in + rb);
             const float4* wsrc = reinterpret_cast<const float4*>(a.w_in + rb);
             const int nq = n >> 2;
-            constexpr int U = 2;                   // float4 pairs in flight (registers)
-            for (int q0 = t; q0 < nq; q0 += U * G) {
-                float4 v[U], u[U];
+            // float4 loads in flight per thread: U of the row, and as many of
+            // the weight when the dual dot is taken on load (registers bound U)
+            auto load_row = [&](auto Uc, auto dotc) {
+                constexpr int U = decltype(Uc)::value;
+                constexpr bool DOT = decltype(dotc)::value;
+                for (int q0 = t; q0 < nq; q0 += U * G) {
+                    float4 v[U], u[U];
 #pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    const int q = q0 + k * G;
-                    v[k] = q < nq ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    u[k] = (q < nq && a.w_in) ? wsrc[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+                    for (int k = 0; k < U; ++k) {
+                        const int q = q0 + k * G;
+                        v[k] = q < nq ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (DOT) u[k] = q < nq ? wsrc[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
 #pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    const int q = q0 + k * G;
-                    if (q < nq) {
-                        float4 x = v[k];
-                        if (a.w_in) {
-                            acc_t_in.add_prod(x.x, u[k].x); acc_t_in.add_prod(x.y, u[k].y);
-                            acc_t_in.add_prod(x.z, u[k].z); acc_t_in.add_prod(x.w, u[k].w);
+                    for (int k = 0; k < U; ++k) {
+                        const int q = q0 + k * G;
+                        if (q < nq) {
+                            float4 x = v[k];
+                            if (DOT) {
+                                acc_t_in.add_prod(x.x, u[k].x); acc_t_in.add_prod(x.y, u[k].y);
+                                acc_t_in.add_prod(x.z, u[k].z); acc_t_in.add_prod(x.w, u[k].w);
+                            }
+                            if (a.negate) { x.x = -x.x; x.y = -x.y; x.z = -x.z; x.w = -x.w; }
+                            f[SK::f(4 * q)] = x.x;     f[SK::f(4 * q + 1)] = x.y;
+                            f[SK::f(4 * q + 2)] = x.z; f[SK::f(4 * q + 3)] = x.w;
                         }
-                        if (a.negate) { x.x = -x.x; x.y = -x.y; x.z = -x.z; x.w = -x.w; }
-                        f[SK::f(4 * q)] = x.x;     f[SK::f(4 * q + 1)] = x.y;
-                        f[SK::f(4 * q + 2)] = x.z; f[SK::f(4 * q + 3)] = x.w;
                     }
                 }
-            }
+            };
+            if (a.w_in) load_row(std::integral_constant<int, 2>(), std::true_type());
+            else        load_row(std::integral_constant<int, 4>(), std::false_type());
         } else {
             for (int p0 = t; p0 < n; p0 += kU * G) {
                 T v[kU], u[kU];
