@@ -68,14 +68,14 @@ def transpose_bytes_per_cell(launches_per_iter: float) -> float:
 # solve, whose summary sits under profiles/); reported only while the
 # kernel source still matches the one the counters were taken on
 TRAFFIC = {
-    # second sweeps (rows of a transposed field, no dot): mean of 5 launches
-    "ct_pass_axis1": {"bytes": 67175577.6 + 11713536.0,
+    # second sweeps (rows of a transposed field, no dot): mean of 4 launches
+    "ct_pass_axis1": {"bytes": 67180544.0 + 8858688.0,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "aa1b97b73ffd6cdea77781c0c2e3e9dd675db80c12c42d320032017c42bba6b9"},
+                      "sha256": "b434e88c1a4de048c9e7b91b6f1d662c31687e1da7b2a8072d6dcc9cbf4b51b9"},
     # first sweeps (with the dual dot on load): mean of 4 launches
-    "ct_pass_axis0": {"bytes": 134847936.0 + 25598976.0,
+    "ct_pass_axis0": {"bytes": 134922624.0 + 23691392.0,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "aa1b97b73ffd6cdea77781c0c2e3e9dd675db80c12c42d320032017c42bba6b9"},
+                      "sha256": "b434e88c1a4de048c9e7b91b6f1d662c31687e1da7b2a8072d6dcc9cbf4b51b9"},
 }
 
 
