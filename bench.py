@@ -588,18 +588,27 @@ def main():
         outs = {"phi": torch.empty(mu_h.shape, dtype=torch.float32).pin_memory().numpy(),
                 "psi": torch.empty(mu_h.shape, dtype=torch.float32).pin_memory().numpy(),
                 "map": torch.empty((2,) + mu_h.shape, dtype=torch.float32).pin_memory().numpy()}
-        t0 = time.perf_counter()
-        re = B.bfm_solve_host(mu_p.numpy(), nu_p.numpy(), tol=args.tol, max_iter=2000,
-                              with_map=True, out=outs)
-        te = time.perf_counter() - t0
+        # one short untimed call first (the workspace's first allocation and
+        # the library's first launches of this grid), then three whole solves
+        B.bfm_solve_host(mu_p.numpy(), nu_p.numpy(), tol=args.tol, max_iter=8, with_map=True,
+                         out=outs)
+        secs, iters = [], []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            re = B.bfm_solve_host(mu_p.numpy(), nu_p.numpy(), tol=args.tol, max_iter=2000,
+                                  with_map=True, out=outs)
+            secs.append(time.perf_counter() - t0)
+            iters.append(re["iters"])
+        te, it_all = sum(secs), sum(iters)
         h2d = 2 * N * 4
         d2h = (2 + 2) * N * 4 + 3 * 8 * (re["iters"] + 1)
-        line["e2e"] = {"value": re["iters"] / te, "unit": UNIT,
+        line["e2e"] = {"value": it_all / te, "unit": UNIT,
                        "h2d_bytes_per_step": h2d / max(re["iters"], 1),
                        "d2h_bytes_per_step": d2h / max(re["iters"], 1),
-                       "seconds_per_solve": te, "iters_per_solve": re["iters"],
+                       "seconds_per_solve": secs, "iters_per_solve": iters,
                        "h2d_bytes_per_solve": h2d, "d2h_bytes_per_solve": d2h,
-                       "call": "bfm_solve_host (pinned host mu, nu -> pinned phi, psi, map), tol 1e-3"}
+                       "call": "bfm_solve_host (pinned host mu, nu -> pinned phi, psi, map), tol 1e-3; "
+                               "three solves after one short untimed call"}
         # ---- the other workloads: 3D, batched uneven solves, the W2^2 loss ---------------
         if not args.no_workloads:
             line["workloads"] = other_workloads(B, dev, stream, args)
