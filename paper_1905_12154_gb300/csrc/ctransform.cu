@@ -64,6 +64,7 @@ struct CtArgs {
     int lw;               // log2(W); interleaved tiles have W a power of two
     int ioff;             // row kernel: byte offset of the int scratch in shared memory
     int soff;             // row kernel on interleaved tiles: byte offset of the output tile
+    int* ctr;             // row kernel on rows: [0] next row to take, [1] groups finished
 };
 
 // Shared-memory layout of a line: thread t owns cells [tK, tK+K).  Stored
@@ -890,9 +891,30 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
         }
         cp_async_commit();
     };
-    if (COLS && prefetch && item0 < nitems) issue_tile(item0, fs);
+    // With a counter (solver launches), lines are handed out as they are
+    // needed: each row group takes its next row when done with the last (rows),
+    // each CTA its next tile one tile ahead, for the prefetch (COLS), so the
+    // groups or CTAs that drew cheap lines take more and no SM idles while
+    // others finish a fixed share.  The last group or CTA to finish resets
+    // the counter for the next launch.
+    const bool dyn = !COLS && !BATCHED && a.ctr != nullptr;
+    const bool dync = COLS && !BATCHED && a.ctr != nullptr && prefetch;
+    __shared__ int row_take[16];                   // one per group (W <= 16)
+    auto take_row = [&]() -> long long {
+        if (t == 0) row_take[w] = atomicAdd(a.ctr, 1);
+        group_sync(w, G);
+        return row_take[w];
+    };
+    long long first = item0, nxt_item = 0;
+    if (dync) {
+        if (tid == 0) row_take[0] = atomicAdd(a.ctr, 1);
+        __syncthreads();
+        first = row_take[0];
+    }
+    if (COLS && prefetch && first < nitems) issue_tile(first, fs);
 
-    for (long long item = item0; item < nitems; item += istep) {
+    for (long long item = dyn ? take_row() : first; item < nitems;
+         item = dyn ? take_row() : (dync ? nxt_item : item + istep)) {
         const long long rb = COLS ? 0 : item * n;
         Tile tl;
         bool active = true;
@@ -903,11 +925,13 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
             active = w < tl.wact;
             f = fs + (size_t)w * a.LD;
             if (prefetch) {
+                if (dync && tid == 0) row_take[1] = atomicAdd(a.ctr, 1);   // the tile after this one
                 cp_async_wait_all();
                 __syncthreads();
                 // the other buffer held the tile before this one, whose
                 // groups all passed the barrier before its store
-                if (item + istep < nitems) issue_tile(item + istep, fs_next);
+                nxt_item = dync ? (long long)row_take[1] : item + istep;
+                if (nxt_item < nitems) issue_tile(nxt_item, fs_next);
             } else {
             const int lw = a.lw, total = n << lw, nth = (int)blockDim.x;
             for (int e0 = tid; e0 < total; e0 += kU * nth) {
@@ -1297,6 +1321,15 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
         if constexpr (!COLS) group_sync(w, G);   // the next row overwrites this group's arrays
         if (prefetch) { T* tb = fs; fs = fs_next; fs_next = tb; }
     }
+    if ((dyn && t == 0) || (dync && tid == 0)) {
+        __threadfence();                           // this group's (CTA's) takes precede its count
+        const int takers = dyn ? (int)(gridDim.x * W) : (int)gridDim.x;
+        if (atomicAdd(a.ctr + 1, 1) == takers - 1) {
+            a.ctr[0] = 0;
+            a.ctr[1] = 0;
+            __threadfence();
+        }
+    }
     if (a.part_in) {
         const double s = block_sum(acc_in, red);
         if (threadIdx.x == 0) a.part_in[blockIdx.x] = s;
@@ -1680,6 +1713,7 @@ static CtArgs<T> make_ct_args(const Grid& g, int axis, const CtPlan& p, const T*
     while ((1 << a.lw) < p.W) ++a.lw;
     a.ioff = p.ioff;
     a.soff = p.soff;
+    a.ctr = nullptr;
     return a;
 }
 
@@ -1716,12 +1750,13 @@ int ct_pass_blocks(const Grid& g, int axis, int elem_bytes, int max_blocks)
 template <typename T>
 bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool negate,
                           const T* w_in, double* part_in, const T* w_out, double* part_out,
-                          const int* done, int max_blocks, cudaStream_t st, int* blocks_used)
+                          const int* done, int max_blocks, cudaStream_t st, int* blocks_used, int* row_ctr)
 {
     if (use_row_kernel(g, axis, (int)sizeof(T))) {
         CtPlan p = plan_ct_row(g, axis, (int)sizeof(T));
         CtArgs<T> a = make_ct_args<T>(g, axis, p, in, out, negate, w_in, part_in, w_out, part_out,
                                       done);
+        a.ctr = row_ctr;
         void* k = row_kernel_for<T>(p.K, false, axis > 0);
         BFM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
         const int blocks = ct_pass_blocks(g, axis, (int)sizeof(T), max_blocks);
@@ -1806,9 +1841,9 @@ template bfm_status launch_ct_pass_batched<float>(const Grid&, int, int, const v
 template bfm_status launch_ct_pass_batched<double>(const Grid&, int, int, const void*, cudaStream_t);
 template bfm_status launch_ct_pass<float>(const Grid&, int, const float*, float*, bool, const float*,
                                           double*, const float*, double*, const int*, int,
-                                          cudaStream_t, int*);
+                                          cudaStream_t, int*, int*);
 template bfm_status launch_ct_pass<double>(const Grid&, int, const double*, double*, bool,
                                            const double*, double*, const double*, double*,
-                                           const int*, int, cudaStream_t, int*);
+                                           const int*, int, cudaStream_t, int*, int*);
 
 }  // namespace bfm

@@ -53,12 +53,15 @@ CtPlan plan_ct_pass(const Grid& g, int axis, int elem_bytes);          // tuned 
 CtPlan plan_ct_pass_default(const Grid& g, int axis, int elem_bytes);  // hand-picked shape
 DctPlan plan_dct_pass(const Grid& g, int axis, int elem_bytes);
 
-// number of CTAs (= partial sums) launch_ct_pass uses for this pass
+// number of CTAs (= partial sums) launch_ct_pass uses for this pass.  row_ctr
+// (optional, device, two ints that are 0 between launches): rows of the row
+// kernel are handed out by an atomic counter instead of a fixed stride
 int ct_pass_blocks(const Grid& g, int axis, int elem_bytes, int max_blocks);
 template <typename T>
 bfm_status launch_ct_pass(const Grid& g, int axis, const T* in, T* out, bool negate,
                           const T* w_in, double* part_in, const T* w_out, double* part_out,
-                          const int* done, int max_blocks, cudaStream_t st, int* blocks_used);
+                          const int* done, int max_blocks, cudaStream_t st, int* blocks_used,
+                          int* row_ctr = nullptr);
 
 bool fft_radices(int n, FftRadices* rs);
 size_t axis_table_bytes(int n, int elem_bytes);

@@ -97,6 +97,8 @@ __global__ void init_state_kernel(SolverState* st, double sigma0, double tol, in
     st->beta1 = b1; st->beta2 = b2; st->alpha1 = a1; st->alpha2 = a2; st->sigma_min = smin;
     st->iter = 0;
     st->done = 0;
+    st->row_ctr[0] = 0;
+    st->row_ctr[1] = 0;
     st->converged = 0;
     st->nonfinite = 0;
     st->pend = 0;
@@ -286,7 +288,7 @@ static bfm_status transpose(const Grid& g, bool forward, const T* in, T* out, co
 template <typename T>
 static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_src, const T* w_out,
                                double* p_in, int* n_in, double* p_out, int* n_out, const int* done,
-                               cudaStream_t st, T* xt, const double* pc)
+                               cudaStream_t st, T* xt, const double* pc, int* row_ctr)
 {
     if (pc) {
         // separable power cost: every axis by the divide-and-conquer pass (columns
@@ -310,7 +312,7 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
         {
             ProfScope ps(PK_CT0, 1, st);
             s = launch_ct_pass<T>(g, 0, src, out, true, w_src, p_in, nullptr, nullptr, done,
-                                  kMaxPartials, st, n_in);
+                                  kMaxPartials, st, n_in, row_ctr);
             if (s != BFM_OK) return s;
         }
         s = transpose<T>(g, true, out, xt, nullptr, nullptr, nullptr, done, st);
@@ -318,7 +320,7 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
         {
             ProfScope ps(PK_CT1, 1, st);
             s = launch_ct_pass<T>(transposed_grid(g), 0, xt, xt, false, nullptr, nullptr, nullptr,
-                                  nullptr, done, kMaxPartials, st, nullptr);
+                                  nullptr, done, kMaxPartials, st, nullptr, row_ctr);
             if (s != BFM_OK) return s;
         }
         return transpose<T>(g, false, xt, out, w_out, p_out, n_out, done, st);
@@ -330,7 +332,7 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
         bfm_status s = launch_ct_pass<T>(g, a, first ? src : out, out, first,
                                          first ? w_src : nullptr, first ? p_in : nullptr,
                                          last ? w_out : nullptr, last ? p_out : nullptr, done,
-                                         kMaxPartials, st, &used);
+                                         kMaxPartials, st, &used, row_ctr);
         if (s != BFM_OK) return s;
         if (first) *n_in = used;
         if (last) *n_out = used;
@@ -345,20 +347,20 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
 // dot of the output is taken by the next sweep that reads it.
 template <typename T>
 static bfm_status ct_flip(const Grid& g, const T* src, T* out, const T* w_src, double* p_in,
-                          int* n_in, const int* done, cudaStream_t st, T* scratch)
+                          int* n_in, const int* done, cudaStream_t st, T* scratch, int* row_ctr)
 {
     bfm_status s;
     {
         ProfScope ps(PK_CT0, 1, st);
         s = launch_ct_pass<T>(g, 0, src, scratch, true, w_src, p_in, nullptr, nullptr, done,
-                              kMaxPartials, st, n_in);
+                              kMaxPartials, st, n_in, row_ctr);
         if (s != BFM_OK) return s;
     }
     s = transpose<T>(g, true, scratch, out, nullptr, nullptr, nullptr, done, st);
     if (s != BFM_OK) return s;
     ProfScope ps(PK_CT1, 1, st);
     return launch_ct_pass<T>(transposed_grid(g), 0, out, out, false, nullptr, nullptr, nullptr,
-                             nullptr, done, kMaxPartials, st, nullptr);
+                             nullptr, done, kMaxPartials, st, nullptr, row_ctr);
 }
 
 // Forward transforms of f = base - in up to (and including) the middle pass;
@@ -459,7 +461,7 @@ static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half,
     int ni = 0, no = 0, ng = 0;
     bfm_status s;
     s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xg,
-                        nullptr);
+                        nullptr, w->state->row_ctr);
     if (s != BFM_OK) return s;
     {
         // the previous half step's flip swept the other layout's rows first
@@ -484,7 +486,7 @@ static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half,
     }
     s = poisson_inverse<T>(g, tabs, rho, src, src, &w->state->sigma, done, st);
     if (s != BFM_OK) return s;
-    return ct_flip<T>(g, src, dst, w_src, slot(w, 3), &ni, done, st, xt);
+    return ct_flip<T>(g, src, dst, w_src, slot(w, 3), &ni, done, st, xt, w->state->row_ctr);
 }
 
 template <typename T>
@@ -509,7 +511,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     bfm_status s;
     T* xt = (T*)w->xt;
     if (w->mu_t && !pc) return half_step_flipped<T>(g, w, phi_half, phi, psi, logs, st);
-    s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc);
+    s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc, w->state->row_ctr);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -531,7 +533,7 @@ bfm_status half_step(const Grid& g, Workspace* w, bool phi_half, T* phi, T* psi,
     }
     s = poisson_inverse<T>(g, w->tabs, rho, src, src, &w->state->sigma, done, st);
     if (s != BFM_OK) return s;
-    s = ct_with_dots<T>(g, src, dst, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc);
+    s = ct_with_dots<T>(g, src, dst, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc, w->state->row_ctr);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -575,7 +577,7 @@ static bfm_status ascent_step(const Grid& g, Workspace* w, T* phi, Logs logs, cu
     }
     s = poisson_inverse<T>(g, w->tabs, rho, phi, phi, &w->state->sigma, done, st);
     if (s != BFM_OK) return s;
-    s = ct_with_dots<T>(g, phi, tmp, nu, mu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc);
+    s = ct_with_dots<T>(g, phi, tmp, nu, mu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc, w->state->row_ctr);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -583,7 +585,7 @@ static bfm_status ascent_step(const Grid& g, Workspace* w, T* phi, Logs logs, cu
                                                         3, logs);
         BFM_LAUNCH_CHECK("finalize_dual_kernel");
     }
-    s = ct_with_dots<T>(g, tmp, phi, mu, nu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc);
+    s = ct_with_dots<T>(g, tmp, phi, mu, nu, slot(w, 0), &ni, slot(w, 1), &no, done, st, xt, pc, w->state->row_ctr);
     if (s != BFM_OK) return s;
     {
         ProfScope ps(PK_SMALL, 1, st);
@@ -678,7 +680,7 @@ bfm_status init_impl(const T* mu, const T* nu, const Grid& g, double tol, int ma
         // the ascent keeps psi_n = phi_n^c in tmp; measure J(phi_0)
         int ni = 0, no = 0;
         s = ct_with_dots<T>(g, phi, (T*)w.tmp, (const T*)w.nu_n, (const T*)w.mu_n, slot(&w, 0), &ni,
-                            slot(&w, 1), &no, &w.state->done, st, (T*)w.xt, pc);
+                            slot(&w, 1), &no, &w.state->done, st, (T*)w.xt, pc, w.state->row_ctr);
         if (s != BFM_OK) return s;
         finalize_dual_kernel<<<1, kFinThreads, 0, st>>>(w.state, slot(&w, 0), ni, slot(&w, 1), no,
                                                         1.0 / (double)g.N, 0, logs);
@@ -825,7 +827,7 @@ bfm_status finish_impl(const Grid& g, int max_iter, unsigned char* wsp, cudaStre
     // even when the loop stopped inside a half step)
     int nd0 = 0, nd1 = 0;
     s = ct_with_dots<T>(g, phi, psi, nullptr, nullptr, nullptr, &nd0, nullptr, &nd1, nullptr, st,
-                        (T*)w.xt, pc);
+                        (T*)w.xt, pc, w.state->row_ctr);
     if (s != BFM_OK) return s;
     if (out->map) { s = launch_map<T>(g, psi, (T*)out->map, st, pc); if (s != BFM_OK) return s; }
     const int nlog = hs.iter + 1;

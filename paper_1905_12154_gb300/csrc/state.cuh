@@ -27,6 +27,7 @@ struct SolverState {
                               // value (flipped layout: see finalize_dual_pend_kernel)
     int power;                // separable power cost with exponents cost_p
     double cost_p[3];
+    int row_ctr[2];           // row c-transform: next row to take, groups done (0 between launches)
 };
 
 struct Logs {
