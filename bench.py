@@ -45,16 +45,15 @@ BYTES_PER_CELL_2D = {
     "dct_inv": 12,         # read spectrum, read potential, write potential
     "pushforward": 16,     # zero rho, read psi, read mu, write rho
 }
-# Long columns (4096^2): the axis-1 sweeps run along the rows of a transposed
-# copy.  The row sweep then reads and writes (8 bytes); the dual dot of the
-# c-transform output moves into the transpose back, so of the 12 transposes of
-# an iteration 4 read a weight as well (8 x 8 + 4 x 12 bytes).
-# Long columns: the second sweep of a c-transform runs along rows of a
-# transposed field and takes no dot (read, write).  Of the L transposes per
-# iteration, 4 belong to the two Poisson solves and one to each c-transform;
-# a c-transform with a second one (back to its input's layout) takes the dot
-# of its output there (L - 8 of them); the others leave their output
-# transposed and its dot to the next sweep that reads it.
+# Long columns (4096^2): the second sweep of a c-transform runs along the rows
+# of a transposed field and takes no dot (read, write).  Of the L transposes
+# per iteration, 4 belong to the two Poisson solves and one to each
+# c-transform, which leaves its output transposed: the pushforward reads
+# psi~ there and takes its dot with mu on the way (L = 8), and the potential's
+# own c-transform leaves its dot to the next sweep that reads it.  Where the
+# transposed rows do not allow the pushforward's row form (n % 4 != 0), the
+# c-transform before it transposes back and takes the dot there (L - 8 of
+# the L transposes read a weight as well).
 BYTES_PER_CELL_2D_TRANSPOSED = dict(BYTES_PER_CELL_2D, ct_pass_axis1=8)
 
 

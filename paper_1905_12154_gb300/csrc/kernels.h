@@ -84,6 +84,12 @@ bfm_status launch_dct_pass(const Grid& g, int axis, int mode, const AxisTables* 
 template <typename T>
 bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho,
                               const int* done, cudaStream_t st, const double* p = nullptr);
+// 2-D: psi~ and mu in the transposed layout (gt), rho out in g's layout;
+// part: per-CTA FP64 partials of <psi~, mu> (their number in *blocks_used)
+template <typename T>
+bfm_status launch_pushforward_t(const Grid& gt, const T* psi_t, const T* mu_t, T* rho,
+                                const Grid& g, const int* done, cudaStream_t st, double* part,
+                                int* blocks_used);
 template <typename T>
 bfm_status launch_map(const Grid& g, const T* psi, T* map, cudaStream_t st,
                       const double* p = nullptr);

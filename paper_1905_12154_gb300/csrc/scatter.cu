@@ -228,11 +228,18 @@ struct StencilAcc {
 // neighbour rows already hold a thread's registers)
 template <int NDIM> __host__ __device__ constexpr int push_vecs() { return NDIM == 2 ? 2 : 1; }
 
-template <typename T, int NDIM>
+// SWAP (2-D): psi and mu come in the transposed layout of rho's grid `go`
+// (g is that transposed grid); each target position is swapped to go's axes
+// before it is deposited, so rho comes out in go's layout with no transpose.
+// part (optional): per-CTA FP64 partial sums of psi * mu (the second term of
+// the dual value, eq. defJ / defI), taken from the loads the map needs: each
+// item's few cells summed in the field precision, the items in FP64.
+template <typename T, int NDIM, bool SWAP>
 __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restrict__ psi,
                                                                const T* __restrict__ mu,
                                                                T* __restrict__ rho, GridDev g,
-                                                               int per_row, const int* done)
+                                                               int per_row, const int* done,
+                                                               GridDev go, double* part)
 {
     if (done && *done) return;
     using VT = typename Vec16<T>::type;
@@ -255,6 +262,7 @@ __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restri
     };
     unsigned it = blockIdx.x * blockDim.x + threadIdx.x;
     if (it < items) load_mu(it);
+    double dsum = 0.0;
     for (; it < items; it += stride) {
         const unsigned row = it / (unsigned)per_row;
         const int x0 = (int)(it - row * (unsigned)per_row) * CW;
@@ -306,17 +314,32 @@ __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restri
         c[0] = x0 > 0 ? psi[base - 1] : (T)0;
         c[CW + 1] = x0 + CW < n0 ? psi[base + CW] : (T)0;
         StencilAcc<T, NDIM> sa;
+        T dot8 = (T)0;                                // this item's cells, then FP64
 #pragma unroll
         for (int k = 0; k < CW; ++k) {
             if (m[k] == (T)0) continue;
+            dot8 = fma(c[k + 1], m[k], dot8);
             T pos[3];
             pos[0] = axis_pos(c[k], c[k + 1], c[k + 2], x0 + k, n0, g.power, g.q[0]);
 #pragma unroll
             for (int a = 1; a < NDIM; ++a)
                 pos[a] = axis_pos(lo[a - 1][k], c[k + 1], hi[a - 1][k], ia[a], g.n[a], g.power, g.q[a]);
-            sa.add(rho, g, pos, m[k]);
+            if (SWAP) {
+                const T p0 = pos[0];
+                pos[0] = pos[1];
+                pos[1] = p0;
+                sa.add(rho, go, pos, m[k]);
+            } else {
+                sa.add(rho, g, pos, m[k]);
+            }
         }
-        sa.flush(rho, g);
+        sa.flush(rho, SWAP ? go : g);
+        dsum += (double)dot8;
+    }
+    if (part) {
+        __shared__ double red[32];
+        const double sb = block_sum(dsum, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = sb;
     }
 }
 
@@ -444,14 +467,46 @@ bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho, 
         long long blr = (items + th - 1) / th;
         const long long cap = (long long)num_sms() * 8;
         if (blr > cap) blr = cap;
-        if (g.ndim == 2) pushforward_rows_kernel<T, 2><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done);
-        else             pushforward_rows_kernel<T, 3><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done);
+        if (g.ndim == 2) pushforward_rows_kernel<T, 2, false><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done, d, nullptr);
+        else             pushforward_rows_kernel<T, 3, false><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done, d, nullptr);
         BFM_LAUNCH_CHECK("pushforward_rows_kernel");
         return BFM_OK;
     }
     if (g.ndim == 2) pushforward_kernel<T, 2><<<bl, th, 0, st>>>(psi, mu, rho, d, done);
     else             pushforward_kernel<T, 3><<<bl, th, 0, st>>>(psi, mu, rho, d, done);
     BFM_LAUNCH_CHECK("pushforward_kernel");
+    return BFM_OK;
+}
+
+// The pushforward of a 2-D quadratic-cost step whose psi~ and mu are held
+// in the transposed layout (gt = transposed_grid(g)): rho comes out in g's
+// layout, and (part) the FP64 partials of <psi~, mu> per CTA, their number in
+// *blocks_used.  Needs the row form's conditions (n % 4, 16-byte alignment).
+template <typename T>
+bfm_status launch_pushforward_t(const Grid& gt, const T* psi_t, const T* mu_t, T* rho,
+                                const Grid& g, const int* done, cudaStream_t st, double* part,
+                                int* blocks_used)
+{
+    const int th = 256;
+    const int CW = Vec16<T>::V * push_vecs<2>();
+    const int per_row = (gt.n[0] + CW - 1) / CW;
+    const long long items = (gt.N / gt.n[0]) * per_row;
+    if (gt.ndim != 2 || g.ndim != 2 || gt.n[0] != g.n[1] || gt.n[1] != g.n[0] || gt.n[0] % 4 != 0 ||
+        !aligned16(psi_t) || !aligned16(mu_t) || !aligned16(rho) || items >= (1ll << 31)) {
+        set_last_error("internal: transposed pushforward needs a 2-D grid, n % 4 == 0 and aligned fields");
+        return BFM_ERR_INVALID_ARG;
+    }
+    BFM_CUDA(cudaMemsetAsync(rho, 0, sizeof(T) * g.N, st));
+    const GridDev dt = dev_grid(gt), dg = dev_grid(g);
+    long long blr = (items + th - 1) / th;
+    const long long cap = (long long)num_sms() * 8;
+    if (blr > cap) blr = cap;
+    if (blr > kMaxPartials) blr = kMaxPartials;
+    if (blr < 1) blr = 1;
+    pushforward_rows_kernel<T, 2, true><<<(int)blr, th, 0, st>>>(psi_t, mu_t, rho, dt, per_row, done, dg,
+                                                                 part);
+    BFM_LAUNCH_CHECK("pushforward_rows_kernel");
+    if (blocks_used) *blocks_used = (int)blr;
     return BFM_OK;
 }
 
@@ -483,6 +538,10 @@ template bfm_status launch_pushforward<float>(const Grid&, const float*, const f
                                               const int*, cudaStream_t, const double*);
 template bfm_status launch_pushforward<double>(const Grid&, const double*, const double*, double*,
                                                const int*, cudaStream_t, const double*);
+template bfm_status launch_pushforward_t<float>(const Grid&, const float*, const float*, float*,
+                                                const Grid&, const int*, cudaStream_t, double*, int*);
+template bfm_status launch_pushforward_t<double>(const Grid&, const double*, const double*, double*,
+                                                 const Grid&, const int*, cudaStream_t, double*, int*);
 template bfm_status launch_map<float>(const Grid&, const float*, float*, cudaStream_t, const double*);
 template bfm_status launch_map<double>(const Grid&, const double*, double*, cudaStream_t, const double*);
 template bfm_status launch_interpolate<float>(const Grid&, const float*, const float*, double,

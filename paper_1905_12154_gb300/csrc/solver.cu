@@ -344,10 +344,13 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
 // the rows of src (with the dot of src and w_src on load), one transpose,
 // then the sweep along the rows of the transposed field in place.  2-D
 // quadratic cost only; one transpose instead of the two of ct_with_dots.  The
-// dot of the output is taken by the next sweep that reads it.
+// dot of the output with w_out_t (laid out like out, i.e. transposed) is
+// taken on the last sweep's store when given; else the next sweep that reads
+// the output takes it.
 template <typename T>
 static bfm_status ct_flip(const Grid& g, const T* src, T* out, const T* w_src, double* p_in,
-                          int* n_in, const int* done, cudaStream_t st, T* scratch, int* row_ctr)
+                          int* n_in, const int* done, cudaStream_t st, T* scratch, int* row_ctr,
+                          const T* w_out_t = nullptr, double* p_out = nullptr, int* n_out = nullptr)
 {
     bfm_status s;
     {
@@ -359,8 +362,8 @@ static bfm_status ct_flip(const Grid& g, const T* src, T* out, const T* w_src, d
     s = transpose<T>(g, true, scratch, out, nullptr, nullptr, nullptr, done, st);
     if (s != BFM_OK) return s;
     ProfScope ps(PK_CT1, 1, st);
-    return launch_ct_pass<T>(transposed_grid(g), 0, out, out, false, nullptr, nullptr, nullptr,
-                             nullptr, done, kMaxPartials, st, nullptr, row_ctr);
+    return launch_ct_pass<T>(transposed_grid(g), 0, out, out, false, nullptr, nullptr, w_out_t,
+                             p_out, done, kMaxPartials, st, n_out, row_ctr);
 }
 
 // Forward transforms of f = base - in up to (and including) the middle pass;
@@ -460,8 +463,23 @@ static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half,
     const T* target = phi_half ? nu : mu;
     int ni = 0, no = 0, ng = 0;
     bfm_status s;
-    s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st, xg,
-                        nullptr, w->state->row_ctr);
+    // psi~ = src^c is left in the transposed layout (in xt), where the
+    // pushforward reads it together with the transposed copy of the source
+    // density and deposits rho in g's layout: no transpose back (where the
+    // transposed rows allow the pushforward's row form, else the transpose)
+    const Grid& gtt = phi_half ? gt : g0;                // the transposed layout of g
+    T* source_t = (T*)(phi_half ? w->mu_t : w->nu_n);
+    // (the pushforward also takes the dot <psi~, mu> from its loads)
+    const bool tpush = xg && gtt.n[0] % 4 == 0;
+    if (tpush) {
+        s = ct_flip<T>(g, src, xt, w_src, slot(w, 0), &ni, done, st, tmp, w->state->row_ctr);
+        if (s != BFM_OK) return s;
+        ProfScope ps(PK_PUSH, 1, st);
+        s = launch_pushforward_t<T>(gtt, xt, source_t, rho, g, done, st, slot(w, 1), &no);
+    } else {
+        s = ct_with_dots<T>(g, src, tmp, w_src, w_dst, slot(w, 0), &ni, slot(w, 1), &no, done, st,
+                            xg, nullptr, w->state->row_ctr);
+    }
     if (s != BFM_OK) return s;
     {
         // the previous half step's flip swept the other layout's rows first
@@ -472,7 +490,7 @@ static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half,
                                                              phi_half ? 0 : 2, logs);
         BFM_LAUNCH_CHECK("finalize_dual_pend_kernel");
     }
-    {
+    if (!tpush) {
         ProfScope ps(PK_PUSH, 1, st);
         s = launch_pushforward<T>(g, tmp, source, rho, done, st, nullptr);
         if (s != BFM_OK) return s;
