@@ -235,11 +235,11 @@ template <int NDIM> __host__ __device__ constexpr int push_vecs() { return NDIM 
 // the dual value, eq. defJ / defI), taken from the loads the map needs: each
 // item's few cells summed in the field precision, the items in FP64.
 template <typename T, int NDIM, bool SWAP>
-__global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restrict__ psi,
-                                                               const T* __restrict__ mu,
-                                                               T* __restrict__ rho, GridDev g,
-                                                               int per_row, const int* done,
-                                                               GridDev go, double* part)
+__device__ __forceinline__ void pushforward_rows_body(const T* __restrict__ psi,
+                                                      const T* __restrict__ mu,
+                                                      T* __restrict__ rho, const GridDev& g,
+                                                      int per_row, const int* done,
+                                                      const GridDev& go, double* part)
 {
     if (done && *done) return;
     using VT = typename Vec16<T>::type;
@@ -341,6 +341,24 @@ __global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restri
         const double sb = block_sum(dsum, red);
         if (threadIdx.x == 0) part[blockIdx.x] = sb;
     }
+}
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) pushforward_rows_kernel(const T* __restrict__ psi,
+                                                               const T* __restrict__ mu,
+                                                               T* __restrict__ rho, GridDev g,
+                                                               int per_row, const int* done)
+{
+    pushforward_rows_body<T, NDIM, false>(psi, mu, rho, g, per_row, done, g, nullptr);
+}
+
+// the transposed form (three CTAs per SM in FP32: 80 registers, no spills)
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+pushforward_rows_t_kernel(const T* __restrict__ psi, const T* __restrict__ mu, T* __restrict__ rho,
+                          GridDev g, int per_row, const int* done, GridDev go, double* part)
+{
+    pushforward_rows_body<T, 2, true>(psi, mu, rho, g, per_row, done, go, part);
 }
 
 // Batched pushforward: blockIdx.y selects the problem.
@@ -467,8 +485,8 @@ bfm_status launch_pushforward(const Grid& g, const T* psi, const T* mu, T* rho, 
         long long blr = (items + th - 1) / th;
         const long long cap = (long long)num_sms() * 8;
         if (blr > cap) blr = cap;
-        if (g.ndim == 2) pushforward_rows_kernel<T, 2, false><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done, d, nullptr);
-        else             pushforward_rows_kernel<T, 3, false><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done, d, nullptr);
+        if (g.ndim == 2) pushforward_rows_kernel<T, 2><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done);
+        else             pushforward_rows_kernel<T, 3><<<(int)blr, th, 0, st>>>(psi, mu, rho, d, per_row, done);
         BFM_LAUNCH_CHECK("pushforward_rows_kernel");
         return BFM_OK;
     }
@@ -503,9 +521,8 @@ bfm_status launch_pushforward_t(const Grid& gt, const T* psi_t, const T* mu_t, T
     if (blr > cap) blr = cap;
     if (blr > kMaxPartials) blr = kMaxPartials;
     if (blr < 1) blr = 1;
-    pushforward_rows_kernel<T, 2, true><<<(int)blr, th, 0, st>>>(psi_t, mu_t, rho, dt, per_row, done, dg,
-                                                                 part);
-    BFM_LAUNCH_CHECK("pushforward_rows_kernel");
+    pushforward_rows_t_kernel<T><<<(int)blr, th, 0, st>>>(psi_t, mu_t, rho, dt, per_row, done, dg, part);
+    BFM_LAUNCH_CHECK("pushforward_rows_t_kernel");
     if (blocks_used) *blocks_used = (int)blr;
     return BFM_OK;
 }
