@@ -129,10 +129,11 @@ __global__ void finalize_dual_pend_kernel(SolverState* st, const double* pprev, 
                                           double hd, int mode, Logs logs)
 {
     if (st->done) return;
-    __shared__ double red[32];
-    const double a = block_sum_parts(pin, nin, red);
-    const double b = block_sum_parts(pout, nout, red);
-    const double c = st->pend ? block_sum_parts(pprev, nprev, red) : 0.0;
+    __shared__ double red[96];
+    double a = thread_sum_parts(pin, nin);
+    double b = thread_sum_parts(pout, nout);
+    double c = st->pend ? thread_sum_parts(pprev, nprev) : 0.0;
+    block_sum3(a, b, c, red);
     if (threadIdx.x == 0) {
         if (st->pend) finalize_dual_body(st, hd * (c + a), mode == 0 ? 3 : 1, logs);
         if (!st->done) finalize_dual_body(st, hd * (a + b), mode, logs);

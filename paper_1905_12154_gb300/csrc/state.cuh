@@ -76,11 +76,43 @@ const double* cost_exponents(const bfm_options* o);
 // ---------------------------------------------------------------------------
 // device-side scalar logic of one half step (run by one thread)
 // ---------------------------------------------------------------------------
+// this thread's share of the n partials, four loads in flight
+__device__ __forceinline__ double thread_sum_parts(const double* p, int n)
+{
+    const int bd = (int)blockDim.x;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int i = (int)threadIdx.x;
+    for (; i + 3 * bd < n; i += 4 * bd) {
+        v0 += p[i];
+        v1 += p[i + bd];
+        v2 += p[i + 2 * bd];
+        v3 += p[i + 3 * bd];
+    }
+    for (; i < n; i += bd) v0 += p[i];
+    return (v0 + v1) + (v2 + v3);
+}
+
 __device__ __forceinline__ double block_sum_parts(const double* p, int n, double* red)
 {
-    double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
-    return block_sum(v, red);
+    return block_sum(thread_sum_parts(p, n), red);
+}
+
+// three block sums with one pair of barriers (all threads call; the totals
+// are valid on thread 0); red holds 96 doubles
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    __syncthreads();
+    if (lane == 0) { red[wid] = a; red[32 + wid] = b; red[64 + wid] = c; }
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    a = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    b = (threadIdx.x < nw) ? red[32 + threadIdx.x] : 0.0;
+    c = (threadIdx.x < nw) ? red[64 + threadIdx.x] : 0.0;
+    if (wid == 0) { a = warp_sum(a); b = warp_sum(b); c = warp_sum(c); }
 }
 
 __device__ __forceinline__ double step_rule(const SolverState* st, double sigma, double gain, double G)
