@@ -67,14 +67,14 @@ def transpose_bytes_per_cell(launches_per_iter: float) -> float:
 # solve, whose summary sits under profiles/); reported only while the
 # kernel source still matches the one the counters were taken on
 TRAFFIC = {
-    # second sweeps (rows of a transposed field, no dot): mean of 4 launches
-    "ct_pass_axis1": {"bytes": 67180544.0 + 8858688.0,
+    # second sweeps (rows of a transposed field, no dot): mean of 6 launches
+    "ct_pass_axis1": {"bytes": 67218474.7 + 9094570.7,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "b434e88c1a4de048c9e7b91b6f1d662c31687e1da7b2a8072d6dcc9cbf4b51b9"},
-    # first sweeps (with the dual dot on load): mean of 4 launches
-    "ct_pass_axis0": {"bytes": 134922624.0 + 23691392.0,
+                      "sha256": "1c4d7a4fa5a4c9652bee1ccfd59d30a0e91cf6fa6b89ab8950192e3967f2dc84"},
+    # first sweeps (with the dual dot on load): mean of 8 launches
+    "ct_pass_axis0": {"bytes": 134567520.0 + 21251424.0,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "b434e88c1a4de048c9e7b91b6f1d662c31687e1da7b2a8072d6dcc9cbf4b51b9"},
+                      "sha256": "1c4d7a4fa5a4c9652bee1ccfd59d30a0e91cf6fa6b89ab8950192e3967f2dc84"},
 }
 
 
