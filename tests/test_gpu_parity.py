@@ -478,6 +478,30 @@ def test_solve_long_rows_and_columns_fp32(B, shape):
     assert np.max(np.abs(host(r["psi"]) - want)) <= 4 * np.finfo(np.float32).eps * scale
 
 
+# Long columns whose length is not a multiple of 4 cells: the pushforward's
+# row form cannot read psi~ in the transposed layout, so psi~ goes back to
+# the potential's layout by a transpose (with the dual dot) and the plain
+# pushforward runs there (1458 = 2 x 3^6 cells, FP32 and FP64).
+@pytest.mark.parametrize("shape,dt", [((12, 1458), torch.float32), ((6, 1458), torch.float64)],
+                         ids=["fp32", "fp64"])
+def test_solve_long_columns_not_multiple_of_4(B, shape, dt):
+    mu, nu = long_column_pair(shape, 46)
+    ref = oracle.solve(mu, nu, tol=0.0, max_iter=6)
+    r = B.bfm_solve(dev(mu, dt), dev(nu, dt), tol=0.0, max_iter=6)
+    assert r["iters"] == 6
+    if dt == torch.float64:
+        assert np.max(np.abs(r["dual"] - ref["dual"])) < 1e-12
+        assert np.max(np.abs(host(r["phi"]) - ref["phi"])) < 1e-10
+    else:
+        assert abs(r["w2sq"] - ref["w2sq"]) / ref["w2sq"] < 1e-5
+        assert np.max(np.abs(r["resid"] - ref["resid"])) < 1e-3
+    s = B.BfmSolver(dev(mu, dt), dev(nu, dt), tol=0.0, max_iter=10)
+    B.bfm_profile_begin(200)
+    s.iterate(1)
+    prof = B.bfm_profile_end()
+    assert prof["transpose"][1] == 6                   # 2 + 2 + 1 + 1: psi~ transposed back
+
+
 @pytest.mark.parametrize("shape,transposes", [((288, 2048), 5), ((2048, 2048), 8), ((486, 2048), 5),
                                               ((2048, 288), 0)], ids=str)
 def test_transposes_follow_column_length(B, shape, transposes):
