@@ -7,7 +7,8 @@
 // i.e. the lower envelope of n parabolas of equal curvature.  The paper
 // evaluates it through the Legendre transform and a convex-hull sweep; here
 // the same envelope is built in parallel by a thread group per line (a CTA
-// holds several lines):
+// holds several lines: whole rows, or interleaved tiles of neighbouring
+// columns; in a solve, rows and column tiles are handed out by a counter):
 //   A. each thread builds the envelope of its own K consecutive parabolas
 //      with a stack kept in place over its cells (a parabola b between a and
 //      c is hidden when the a/b crossing lies right of the b/c crossing);

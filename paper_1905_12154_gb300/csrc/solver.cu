@@ -433,9 +433,11 @@ constexpr int kFinThreads = 256;
 // in the grid's layout and psi in the transposed one, so the c-transforms
 // phi -> psi and psi -> phi each leave their output transposed (ct_flip, one
 // transpose) and the psi-half runs on the transposed grid with the
-// transposed copies of mu and nu; the c-transform before each Poisson solve
-// keeps its layout (its output feeds the pushforward and the update of the
-// same potential).  The dual value after the update (J(phi_{n+1/2}) or
+// transposed copies of mu and nu.  The c-transform psi~ before the Poisson
+// solve leaves its output transposed too, where the pushforward reads it and
+// deposits rho in the potential's layout (the layout the Poisson solve and
+// the update share); rows that are not a multiple of 4 cells take the
+// transpose back and the plain pushforward instead.  The dual value after the update (J(phi_{n+1/2}) or
 // I(psi_{n+1})) shares its second term with the measurement that starts the
 // next half step (<psi_{n+1/2}, mu> or <phi_{n+1}, nu>), so its step rule runs
 // there (finalize_dual_pend_kernel), before the measurement and before the
