@@ -70,11 +70,11 @@ TRAFFIC = {
     # second sweeps (rows of a transposed field, no dot): mean of 6 launches
     "ct_pass_axis1": {"bytes": 67218474.7 + 9094570.7,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "1c4d7a4fa5a4c9652bee1ccfd59d30a0e91cf6fa6b89ab8950192e3967f2dc84"},
+                      "sha256": "74de2f878f7f940565d7e14bbee9870626c35733b9620a5250edcc83198ce4de"},
     # first sweeps (with the dual dot on load): mean of 8 launches
     "ct_pass_axis0": {"bytes": 134567520.0 + 21251424.0,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "1c4d7a4fa5a4c9652bee1ccfd59d30a0e91cf6fa6b89ab8950192e3967f2dc84"},
+                      "sha256": "74de2f878f7f940565d7e14bbee9870626c35733b9620a5250edcc83198ce4de"},
 }
 
 
