@@ -346,10 +346,12 @@ bfm_status bfm_interpolate(const void *map, const void *mu, double t, void *rho,
  * (kind): 0 = tile rows (axis 0, lines of at most 256 cells), 1 = tile
  * columns (axes > 0, W neighbouring lines interleaved), 2 = the row kernel
  * (axis 0, rows of more than 256 cells), 3 = the row kernel on interleaved
- * tiles (axes > 0, lines of more than 256 cells whose default tile spans at
- * least 32 bytes per position; longer 2-D columns are transposed and swept
- * as rows, or take kind 1 where no transpose is used).  A shape is (K, W) with W = 0 for
- * "as many lines as fit" (512 threads, about 110 KB of shared memory).
+ * tiles (axes > 0, lines of more than 256 cells where a tile of the default
+ * shape spans at least 32 bytes per element position; longer lines along
+ * axis 1 of a 2-D grid are swept as rows of a transposed copy by the solver,
+ * and take kind 1 in the batched solver and in bfm_ctransform).  A shape is
+ * (K, W) with W = 0 for "as many lines as fit" (512 threads, about 110 KB of
+ * shared memory).
  * Every shape computes the same exact discrete envelope; shapes differ in
  * speed only (and in rounding order where hidden-parabola tests tie).
  * The table of chosen shapes is process-wide, read whenever a pass is
