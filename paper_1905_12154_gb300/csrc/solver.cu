@@ -345,13 +345,11 @@ static bfm_status ct_with_dots(const Grid& g, const T* src, T* out, const T* w_s
 // the rows of src (with the dot of src and w_src on load), one transpose,
 // then the sweep along the rows of the transposed field in place.  2-D
 // quadratic cost only; one transpose instead of the two of ct_with_dots.  The
-// dot of the output with w_out_t (laid out like out, i.e. transposed) is
-// taken on the last sweep's store when given; else the next sweep that reads
-// the output takes it.
+// dot of the output is taken by the kernel that reads it next (a sweep, or
+// the pushforward).
 template <typename T>
 static bfm_status ct_flip(const Grid& g, const T* src, T* out, const T* w_src, double* p_in,
-                          int* n_in, const int* done, cudaStream_t st, T* scratch, int* row_ctr,
-                          const T* w_out_t = nullptr, double* p_out = nullptr, int* n_out = nullptr)
+                          int* n_in, const int* done, cudaStream_t st, T* scratch, int* row_ctr)
 {
     bfm_status s;
     {
@@ -363,8 +361,8 @@ static bfm_status ct_flip(const Grid& g, const T* src, T* out, const T* w_src, d
     s = transpose<T>(g, true, scratch, out, nullptr, nullptr, nullptr, done, st);
     if (s != BFM_OK) return s;
     ProfScope ps(PK_CT1, 1, st);
-    return launch_ct_pass<T>(transposed_grid(g), 0, out, out, false, nullptr, nullptr, w_out_t,
-                             p_out, done, kMaxPartials, st, n_out, row_ctr);
+    return launch_ct_pass<T>(transposed_grid(g), 0, out, out, false, nullptr, nullptr, nullptr,
+                             nullptr, done, kMaxPartials, st, nullptr, row_ctr);
 }
 
 // Forward transforms of f = base - in up to (and including) the middle pass;
@@ -437,11 +435,12 @@ constexpr int kFinThreads = 256;
 // solve leaves its output transposed too, where the pushforward reads it and
 // deposits rho in the potential's layout (the layout the Poisson solve and
 // the update share); rows that are not a multiple of 4 cells take the
-// transpose back and the plain pushforward instead.  The dual value after the update (J(phi_{n+1/2}) or
-// I(psi_{n+1})) shares its second term with the measurement that starts the
-// next half step (<psi_{n+1/2}, mu> or <phi_{n+1}, nu>), so its step rule runs
-// there (finalize_dual_pend_kernel), before the measurement and before the
-// next update uses sigma.  Same steps and step rule as half_step.
+// transpose back and the plain pushforward instead.  The dual value after the
+// update (J(phi_{n+1/2}) or I(psi_{n+1})) shares its second term with the
+// measurement that starts the next half step (<psi_{n+1/2}, mu> or
+// <phi_{n+1}, nu>), so its step rule runs there (finalize_dual_pend_kernel),
+// before the measurement and before the next update uses sigma.  Same steps
+// and step rule as half_step.
 template <typename T>
 static bfm_status half_step_flipped(const Grid& g0, Workspace* w, bool phi_half, T* phi, T* psi,
                                     Logs logs, cudaStream_t st)
