@@ -981,8 +981,13 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
                         if (q < nq) {
                             float4 x = v[k];
                             if (DOT) {
-                                acc_t_in.add_prod(x.x, u[k].x); acc_t_in.add_prod(x.y, u[k].y);
-                                acc_t_in.add_prod(x.z, u[k].z); acc_t_in.add_prod(x.w, u[k].w);
+                                // the vector's four products in FP32, their sum
+                                // into the compensated accumulator
+                                float s4 = x.x * u[k].x;
+                                s4 = fmaf(x.y, u[k].y, s4);
+                                s4 = fmaf(x.z, u[k].z, s4);
+                                s4 = fmaf(x.w, u[k].w, s4);
+                                acc_t_in.add(s4);
                             }
                             if (a.negate) { x.x = -x.x; x.y = -x.y; x.z = -x.z; x.w = -x.w; }
                             f[SK::f(4 * q)] = x.x;     f[SK::f(4 * q + 1)] = x.y;
