@@ -919,17 +919,21 @@ dct_row_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
             const long long ia = ra, ib = ra + 1;
             const float La = a.lam_a0[ia], Lb = hb ? a.lam_a0[ib] : 0.f;
             const float wa = (ia == 0) ? 1.f : 2.f, wb = 2.f;
+            // G's terms are all positive: the (up to four) terms of one pair
+            // (k, n - k) are summed in FP32, that sum into the compensated one
+            float gp = 0.f;
             auto divide = [&](int kk, C v) {
                 const float lk = a.lam_axis[kk];
                 const float wk = (kk == 0) ? 1.f : 2.f;
                 const float la = La + lk, lb = Lb + lk;
                 float ga = 0.f, gb = 0.f;
-                if (la > 0.f) { ga = __fdividef(v.x, la); gsum.add_prod(wa * wk * v.x, ga); }
-                if (hb && lb > 0.f) { gb = __fdividef(v.y, lb); gsum.add_prod(wb * wk * v.y, gb); }
+                if (la > 0.f) { ga = __fdividef(v.x, la); gp = fmaf(wa * wk * v.x, ga, gp); }
+                if (hb && lb > 0.f) { gb = __fdividef(v.y, lb); gp = fmaf(wb * wk * v.y, gb, gp); }
                 v.x = ga; v.y = gb;
                 return v;
             };
             for (int k = t; k <= n / 2; k += T) {
+                gp = 0.f;
                 const int km = (n - k) & (n - 1);
                 const C Zk = z[padix(k)], Zm = z[padix(km)];
                 C A, Bq;
@@ -962,6 +966,7 @@ dct_row_kernel(DctArgs<float> a0, const DctArgs<float>* batch)
                     z[padix(km)] = Zm2;
                 }
                 z[padix(k)] = Zk2;
+                gsum.add(gp);
             }
             acc += gsum.take();
             __syncthreads();
