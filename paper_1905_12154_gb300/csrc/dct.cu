@@ -1247,9 +1247,10 @@ __global__ void __launch_bounds__(512, 2) dct384_kernel(DctArgs<float> a)
                 const float wk = (k == 0) ? 1.f : 2.f;
                 C v = z[padix(k)];
                 const float la = La + lk, lb = Lb + lk;
-                float ga = 0.f, gb = 0.f;
-                if (la > 0.f) { ga = __fdividef(v.x, la); gsum.add_prod(wa * wk * v.x, ga); }
-                if (lb > 0.f) { gb = __fdividef(v.y, lb); gsum.add_prod(wb * wk * v.y, gb); }
+                float ga = 0.f, gb = 0.f, gp = 0.f;      // G's two (positive) terms in FP32
+                if (la > 0.f) { ga = __fdividef(v.x, la); gp = (wa * wk * v.x) * ga; }
+                if (lb > 0.f) { gb = __fdividef(v.y, lb); gp = fmaf(wb * wk * v.y, gb, gp); }
+                gsum.add(gp);
                 v.x = ga; v.y = gb;
                 z[padix(k)] = v;
             }
