@@ -79,6 +79,16 @@ template <int K> struct Skew {
     __device__ __forceinline__ static int s(int p) { return p + 2 * (p >> lg); }
 };
 
+// The four products of a pair of float4 summed in FP32 (one FMA chain): the
+// dual dots add one such sum per vector to their compensated accumulators.
+__device__ __forceinline__ float dot4(const float4 a, const float4 b)
+{
+    float s = a.x * b.x;
+    s = fmaf(a.y, b.y, s);
+    s = fmaf(a.z, b.z, s);
+    return fmaf(a.w, b.w, s);
+}
+
 template <int K, typename T>
 __device__ __forceinline__ bool hidden(const T* f, int a, int b, int c, T hh)
 {
@@ -389,11 +399,7 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
                     const float4* wsrc = reinterpret_cast<const float4*>(a.w_in + rb);
                     for (int q = tid; q < (n >> 2); q += blockDim.x) {
                         float4 v = src[q];
-                        if (a.w_in) {
-                            const float4 u = wsrc[q];
-                            acc_t_in.add_prod(v.x, u.x); acc_t_in.add_prod(v.y, u.y);
-                            acc_t_in.add_prod(v.z, u.z); acc_t_in.add_prod(v.w, u.w);
-                        }
+                        if (a.w_in) acc_t_in.add(dot4(v, wsrc[q]));
                         if (a.negate) { v.x = -v.x; v.y = -v.y; v.z = -v.z; v.w = -v.w; }
                         frow[SK::f(4 * q)] = v.x;     frow[SK::f(4 * q + 1)] = v.y;
                         frow[SK::f(4 * q + 2)] = v.z; frow[SK::f(4 * q + 3)] = v.w;
@@ -620,11 +626,7 @@ __global__ void __launch_bounds__(512, 2) ct_pass_kernel(CtArgs<T> a0, const CtA
                         const float4 v = make_float4(frow[SK::f(4 * q)], frow[SK::f(4 * q + 1)],
                                                      frow[SK::f(4 * q + 2)], frow[SK::f(4 * q + 3)]);
                         dst[q] = v;
-                        if (a.w_out) {
-                            const float4 u = wsrc[q];
-                            acc_t_out.add_prod(v.x, u.x); acc_t_out.add_prod(v.y, u.y);
-                            acc_t_out.add_prod(v.z, u.z); acc_t_out.add_prod(v.w, u.w);
-                        }
+                        if (a.w_out) acc_t_out.add(dot4(v, wsrc[q]));
                     }
                 } else {
                     for (int p = tid; p < n; p += blockDim.x) {
@@ -980,15 +982,7 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
                         const int q = q0 + k * G;
                         if (q < nq) {
                             float4 x = v[k];
-                            if (DOT) {
-                                // the vector's four products in FP32, their sum
-                                // into the compensated accumulator
-                                float s4 = x.x * u[k].x;
-                                s4 = fmaf(x.y, u[k].y, s4);
-                                s4 = fmaf(x.z, u[k].z, s4);
-                                s4 = fmaf(x.w, u[k].w, s4);
-                                acc_t_in.add(s4);
-                            }
+                            if (DOT) acc_t_in.add(dot4(x, u[k]));
                             if (a.negate) { x.x = -x.x; x.y = -x.y; x.z = -x.z; x.w = -x.w; }
                             f[SK::f(4 * q)] = x.x;     f[SK::f(4 * q + 1)] = x.y;
                             f[SK::f(4 * q + 2)] = x.z; f[SK::f(4 * q + 3)] = x.w;
@@ -1103,11 +1097,7 @@ __global__ void __launch_bounds__(512, 2) ct_row_kernel(CtArgs<T> a0, const CtAr
             } else if (sizeof(T) == 4 && a.vec4 && x0 + 4 <= hi) {
                 float4 v4 = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
                 *reinterpret_cast<float4*>(dst + x0) = v4;
-                if (wo) {
-                    const float4 u4 = *reinterpret_cast<const float4*>(wo + x0);
-                    acc_t_out.add_prod(o[0], (T)u4.x); acc_t_out.add_prod(o[1], (T)u4.y);
-                    acc_t_out.add_prod(o[2], (T)u4.z); acc_t_out.add_prod(o[3], (T)u4.w);
-                }
+                if (wo) acc_t_out.add(dot4(v4, *reinterpret_cast<const float4*>(wo + x0)));
             } else {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
