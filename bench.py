@@ -67,14 +67,14 @@ def transpose_bytes_per_cell(launches_per_iter: float) -> float:
 # solve, whose summary sits under profiles/); reported only while the
 # kernel source still matches the one the counters were taken on
 TRAFFIC = {
-    # second sweeps (rows of a transposed field, no dot): mean of 6 launches
-    "ct_pass_axis1": {"bytes": 67218474.7 + 9094570.7,
+    # second sweeps (rows of a transposed field, no dot): mean of 8 launches
+    "ct_pass_axis1": {"bytes": 67178624.0 + 9008736.0,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "74de2f878f7f940565d7e14bbee9870626c35733b9620a5250edcc83198ce4de"},
+                      "sha256": "52a097ee8a64d6968fe09b573982f01697eab83544a0b5727e69c766b74e2782"},
     # first sweeps (with the dual dot on load): mean of 8 launches
-    "ct_pass_axis0": {"bytes": 134567520.0 + 21251424.0,
+    "ct_pass_axis0": {"bytes": 134824576.0 + 23506112.0,
                       "source": "paper_1905_12154_gb300/csrc/ctransform.cu",
-                      "sha256": "74de2f878f7f940565d7e14bbee9870626c35733b9620a5250edcc83198ce4de"},
+                      "sha256": "52a097ee8a64d6968fe09b573982f01697eab83544a0b5727e69c766b74e2782"},
 }
 
 
